@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 generalized-Stokes solver.
+
+Metric: Stokes DOFs solved per second at true relative residual 1e-8, where
+DOFs = 3 (2n+1)^3 + (n+1)^3 (velocity and pressure nodes including the
+boundary, the paper's count for its throughput TPS). Workload: the 48^3-cube
+Kuhn mesh of the unit cube with interior vertices jittered by up to 0.2 h
+(seed 2), P2-P1, dt = 1e-3, mu in {1, 1e-2, 1e-4}, manufactured right-hand side,
+Schur-complement CG with the Cahouet-Chabard preconditioner (C^Lambda).
+One step = one solve for each of the three viscosities. Inputs are resident in
+HBM; every matrix is larger than L2, so no separate L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (launched under torchrun) each rank solves its own replica of the
+workload; value = all ranks' DOFs / the slowest rank's time ("replicas only":
+the method has no data-parallel exchange step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Stokes DOFs solved per second at rel. residual 1e-8"
+UNIT = "DOF/s"
+N_DEFAULT = 48
+MUS = (1.0, 1e-2, 1e-4)
+DT = 1e-3
+JITTER = 0.2
+SEED = 2
+TOL = 1e-8
+CPU_SAMPLE_N = 8
+
+
+def workload_name(n):
+    return f"kuhn{n}^3-jitter0.2-P2P1-dt1e-3-mu{{1,1e-2,1e-4}}-schurCG-CLambda"
+
+
+def config(n, precision):
+    return {"workload": workload_name(n), "n_cubes": n, "mus": list(MUS), "dt": DT,
+            "jitter": JITTER, "seed": SEED, "tol": TOL, "precision": precision,
+            "dofs_per_solve": 3 * (2 * n + 1) ** 3 + (n + 1) ** 3,
+            "solves_per_step": len(MUS), "method": "schur-cg", "schur_prec": "C^Lambda",
+            "l2": "inputs larger than L2 (every matrix > 129 MB), no flush",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_step(n=CPU_SAMPLE_N):
+    import workload as wl
+    from oracle.assemble import StokesSystem
+    from oracle.mesh import KuhnMesh
+    from oracle.solve import oracle_solve, relative_residual
+    V = wl.kuhn_vertices(n, JITTER, SEED)
+    t0 = time.perf_counter()
+    worst = 0.0
+    for mu in MUS:
+        s = StokesSystem(KuhnMesh(n, V), mu, DT)
+        f = wl.manufactured_force(n, V, mu, DT, SEED)
+        F = s.load(f)
+        U, P = oracle_solve(s, F)
+        worst = max(worst, relative_residual(s, U, P, F))
+    return time.perf_counter() - t0, worst
+
+
+def cpu_baseline_worker(steps):
+    times = []
+    worst = 0.0
+    for _ in range(steps):
+        t, w = oracle_step()
+        times.append(t)
+        worst = max(worst, w)
+    dofs = 3 * (2 * CPU_SAMPLE_N + 1) ** 3 + (CPU_SAMPLE_N + 1) ** 3
+    t = statistics.median(times)
+    print(json.dumps({"seconds_per_step": t, "value": len(MUS) * dofs / t, "worst_residual": worst,
+                      "steps": steps}))
+
+
+def run_cpu_baseline(steps=1):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
+                          str(steps)], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "error": out.stderr[-300:]}
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle exact discrete solve (COO assembly + sparse-LU Schur CG to 1e-14) of "
+                       f"the {CPU_SAMPLE_N}^3 jittered instance, mu in {{1,1e-2,1e-4}}, dt=1e-3, "
+                       f"{r['seconds_per_step']:.1f} s per 3 solves; single thread"),
+            "worst_residual": r["worst_residual"]}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.dev), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.send_signal(signal.SIGTERM)
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [x for x in sm if x >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_name):
+    """Per-launch DRAM bytes of `kernel_name` from a committed ncu summary, if the
+    summary was taken on the current kernel source."""
+    src = os.path.join(ROOT, "paper_2407_01783_gb300", "csrc", "sparse.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    prof = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(prof):
+        return None
+    for fn in sorted(os.listdir(prof)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(prof, fn)):
+            m = re.search(r"bench-traffic: kernel=(\w+) bytes_per_launch=([0-9.eE+]+) sparse_cu_sha=(\w+)", line)
+            if m and m.group(1) == kernel_name and m.group(3) == sha:
+                return float(m.group(2))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workload as wl
+    import paper_2407_01783_gb300 as sk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.n
+    V = wl.kuhn_vertices(n, JITTER, SEED)
+    dofs = 3 * (2 * n + 1) ** 3 + (n + 1) ** 3
+    prec = sk.PRECISION_MIXED if args.precision == "mixed" else sk.PRECISION_FP64
+
+    def make(precision, profile):
+        solvers, fs, outs = [], [], []
+        for mu in MUS:
+            opt = sk.stokes_default_options(precision=precision, profile=profile)
+            S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
+            f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
+            u = torch.empty_like(f)
+            p = torch.empty(S.n_p1, dtype=torch.float64, device=dev)
+            solvers.append(S)
+            fs.append(f)
+            outs.append((u, p))
+        return solvers, fs, outs
+
+    def step(solvers, fs, outs, infos):
+        for S, f, (u, p) in zip(solvers, fs, outs):
+            _, _, info = S.solve(f, None, TOL, out=(u, p))
+            infos.append(info.as_dict())
+
+    def timed(solvers, fs, outs, steps, warmup, clocks=None):
+        infos = []
+        for _ in range(warmup):
+            step(solvers, fs, outs, infos)
+        for S in solvers:
+            sk.stokes_kernel_stats_reset(S.ctx)
+        infos = []
+        stream = torch.cuda.current_stream(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        if clocks:
+            clocks.start()
+        e0.record(stream)
+        for _ in range(steps):
+            step(solvers, fs, outs, infos)
+        e1.record(stream)
+        barrier()
+        ck = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, ck
+
+    t_setup = time.perf_counter()
+    solvers, fs, outs = make(prec, 1)
+    torch.cuda.synchronize()
+    setup_s = (time.perf_counter() - t_setup) / len(MUS)
+    clocks = Clocks(local)
+    ms, infos, ck = timed(solvers, fs, outs, args.steps, args.warmup, clocks)
+    worst = max(i["rel_residual"] for i in infos)
+    bad = [i for i in infos if i["status"] != 0]
+    value = world * len(MUS) * dofs / (ms / 1e3)
+
+    # per-kernel CUDA-event statistics over the timed region
+    kinfo = {}
+    total_launches = 0
+    for name, kid in sk.KERNEL.items():
+        cnt, kms, kbytes = 0, 0.0, 0.0
+        for S in solvers:
+            c_, m_, b_ = sk.stokes_kernel_stats(S.ctx, kid)
+            cnt += c_
+            kms += m_
+            kbytes += b_
+        total_launches += cnt
+        kinfo[name] = {"launches": cnt, "ms": kms, "bytes": kbytes}
+    dom = max((k for k in kinfo if k not in ("BLAS1", "OTHER")), key=lambda k: kinfo[k]["ms"])
+    d = kinfo[dom]
+    peak, peak_kind = measured_peak_gbs()
+    achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": ncu_traffic(dom),
+                "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"])}
+    kernels = {k: {"launches_per_step": v["launches"] / args.steps,
+                   "ms_per_step": v["ms"] / args.steps,
+                   "share": v["ms"] / max(1e-12, sum(x["ms"] for x in kinfo.values())),
+                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+               for k, v in kinfo.items()}
+
+    # end to end through the public API with HOST buffers (copies inside the timing)
+    fh = [torch.empty_like(f, device="cpu").pin_memory() for f in fs]
+    for a, b in zip(fh, fs):
+        a.copy_(b)
+    fh_np = [a.numpy() for a in fh]
+    uh = [torch.empty_like(f, device="cpu").pin_memory().numpy() for f in fs]
+    ph = [torch.empty(S.n_p1, dtype=torch.float64).pin_memory().numpy() for S in solvers]
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        for S, f, u, p in zip(solvers, fh_np, uh, ph):
+            sk.stokes_solve_host(S.ctx, f, None, TOL, u, p)
+        barrier()
+        if it >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_step = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    h2d = sum(a.nbytes for a in fh_np)
+    d2h = sum(a.nbytes for a in uh) + sum(a.nbytes for a in ph)
+    for S in solvers:
+        S.close()
+    del solvers
+
+    fp64 = None
+    if prec == sk.PRECISION_MIXED and not args.no_fp64:
+        s2, f2, o2 = make(sk.PRECISION_FP64, 0)
+        ms64, inf64, _ = timed(s2, f2, o2, max(1, args.steps // 2), max(1, args.warmup // 2))
+        fp64 = {"value": world * len(MUS) * dofs / (ms64 / 1e3), "ms_per_step": ms64,
+                "worst_residual": max(i["rel_residual"] for i in inf64),
+                "iters": [(i["outer_iters"], i["inner_iters"], i["refinements"]) for i in inf64[:3]]}
+        for S in s2:
+            S.close()
+
+    if rank != 0:
+        return None
+    cpu = run_cpu_baseline(1) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == sk.PRECISION_MIXED else "f64",
+        "data": "synthetic (seeded jittered Kuhn mesh, manufactured solution)",
+        "config": config(n, args.precision),
+        "clocks": ck,
+        "e2e": {"value": world * len(MUS) * dofs / (e2e_step / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "gpu_launches": int(total_launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "setup_s_per_instance": setup_s,
+        "worst_rel_residual": worst,
+        "failed_solves": len(bad),
+        "iters": [(i["outer_iters"], i["inner_iters"], i["refinements"]) for i in infos[:3]],
+        "kernels": kernels,
+        "plain_fp64": fp64,
+    }
+    return line
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return None
+    for _ in range(args.warmup):
+        oracle_step()
+    ts = []
+    worst = 0.0
+    for _ in range(args.steps):
+        t, w = oracle_step()
+        ts.append(t)
+        worst = max(worst, w)
+    dofs = 3 * (2 * CPU_SAMPLE_N + 1) ** 3 + (CPU_SAMPLE_N + 1) ** 3
+    sec = statistics.mean(ts)
+    value = len(MUS) * dofs / sec
+    sample = (f"oracle exact discrete solve of the {CPU_SAMPLE_N}^3 jittered instance "
+              f"(bounded sample of the {args.n}^3 workload), mu in {{1,1e-2,1e-4}}, dt=1e-3")
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded jittered Kuhn mesh, manufactured solution)",
+            "config": config(args.n, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(threads), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "worst_rel_residual": worst}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--cpu-baseline-worker", type=int, default=0, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_baseline_worker:
+        cpu_baseline_worker(args.cpu_baseline_worker)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

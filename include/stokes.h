@@ -1,0 +1,217 @@
+/*
+ * stokes.h - C ABI of a GB300 (sm_103a) solver for the generalized Stokes
+ * saddle-point system from P2-P1 Taylor-Hood elements on Kuhn tetrahedral
+ * meshes of the unit cube (Creff & Guermond, arXiv 2407.01783).
+ *
+ * The discrete problem (Sec. 2.2, Eq. Saddle_point_A_BT_B, with a pressure
+ * load g added):
+ *     A U - B^T P = F,   B U = g,   int p_h = 0,
+ *     A = M_V/dt + mu E_V  (Eq. for A_ij; E_V from 2 eps(u):eps(v)),
+ *     B_kj = int psi_k div phi_j  (Eq. def_of_Aij_Bij),
+ * optionally in augmented-Lagrangian form A_gamma = A + gamma mu B^T M_Q^{-1} B
+ * (Eqs. LA_problem, def_of_Alambda; the paper's lambda is gamma here).
+ *
+ * Solvers (Sec. 2.3 and 2.4): Method 1 = conjugate gradients on the pressure
+ * Schur complement S = B A^{-1} B^T preconditioned by the Cahouet-Chabard
+ * operator C^Lambda = mu(1+gamma) M_Q^{-1} + dt^{-1} (B Lambda_V^{-1} B^T)^{-1}
+ * (or C^Delta with L_Q in place of B Lambda_V^{-1} B^T; Eqs.
+ * Schur_complement_preconditioners); Method 2 = FGMRES on the coupled system
+ * with the block-LU preconditioner of Eq. inexact_factorization_of_Alambda
+ * (or its block-triangular variant, Remark "Alternative preconditioner").
+ * Velocity solves are preconditioned by V-cycles on A~_3 = M_V/dt + mu L_V
+ * (Eq. precond_A_plus_lambda_D_3).
+ *
+ * Conventions for every entry point:
+ *  - Mesh: n^3 cubes, each split into 6 tetrahedra (one per axis permutation).
+ *    Vertices are (n+1)^3 rows of 3 doubles, lexicographic, x fastest.
+ *  - P2 nodes: the (2n+1)^3 half-grid, lexicographic, x fastest; velocity
+ *    fields are node-interleaved [(2n+1)^3][3]. P1 (pressure) fields are
+ *    [(n+1)^3].
+ *  - Device pointers live in the CUDA context current when stokes_setup was
+ *    called and are used on the stream given there. Functions ending in
+ *    _host take host pointers instead and copy inside the call.
+ *  - The caller owns every array it passes; the context owns all matrices
+ *    and work space and frees them in stokes_destroy.
+ *  - Every call returns a stokes_status; none aborts, traps or prints. On
+ *    error, stokes_last_error() describes the cause (per thread).
+ */
+#ifndef STOKES_H
+#define STOKES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stokes_ctx stokes_ctx;
+
+typedef enum {
+  STOKES_OK = 0,
+  STOKES_ERR_ARG = -1,             /* bad argument (size, pointer, option) */
+  STOKES_ERR_OOM = -2,             /* device allocation failed */
+  STOKES_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+  STOKES_ERR_NOT_CONVERGED = -4,   /* iteration cap hit; best iterate written */
+  STOKES_ERR_BREAKDOWN = -5,       /* Krylov breakdown (p^T A p <= 0 etc.) */
+  STOKES_ERR_NAN = -6,             /* non-finite value in a residual */
+  STOKES_ERR_TIMEOUT = -7,         /* a bounded device wait expired */
+  STOKES_ERR_INCOMPATIBLE_RHS = -8,/* sum(g) != 0: B U = g has no solution */
+  STOKES_ERR_MESH = -9             /* inverted or degenerate tetrahedron */
+} stokes_status;
+
+enum { STOKES_METHOD_SCHUR = 0, STOKES_METHOD_COUPLED = 1 };
+/* Schur-complement preconditioner: C^Lambda (lumped velocity mass, the
+ * paper's recommendation) or C^Delta (pressure Laplacian). */
+enum { STOKES_SCHUR_PREC_LUMPED = 0, STOKES_SCHUR_PREC_LAPLACE = 1 };
+/* FP64 everywhere, or FP32 matrices/multigrid/inner Krylov with FP64 outer
+ * refinement, dot products, pressure-mean projection and coarse factors. */
+enum { STOKES_PRECISION_FP64 = 0, STOKES_PRECISION_MIXED = 1 };
+
+typedef struct {
+  int method;            /* STOKES_METHOD_* */
+  int schur_prec;        /* STOKES_SCHUR_PREC_* */
+  int precision;         /* STOKES_PRECISION_* */
+  int vcycles;           /* V-cycles per A~_3^{-1} application ("2Vc": 2) */
+  int cheb_degree;       /* Chebyshev-Jacobi steps per pre/post smoothing */
+  int mass_steps;        /* Chebyshev steps for (M_Q)^{-1} inside C */
+  int mass_steps_al;     /* Chebyshev steps for M_Q^{-1} inside A_gamma */
+  int restart;           /* FGMRES restart length (Method 2) */
+  int block_lu;          /* Method 2: 1 full block-LU, 0 block-triangular */
+  int m2_inner_cg;       /* Method 2: 1 = A~^{-1} by PCG to inner_tol, 0 = V-cycles */
+  double inner_tol;      /* relative tolerance of inner velocity solves */
+  double schur_inner_tol;/* relative tolerance of the pressure-operator solve in C */
+  double eps_pressure;   /* eps of eps M_Q + L_Q (the paper uses 1) */
+  int max_outer;         /* outer Krylov iterations per refinement pass */
+  int max_inner;         /* inner Krylov iterations per solve */
+  int max_refine;        /* refinement passes on the full FP64 residual */
+  int profile;           /* 1: record per-kernel CUDA-event timings */
+  int spmv_group;        /* threads per sparse row: 0 autotune, else 1..32 */
+} stokes_options;
+
+typedef struct {
+  int outer_iters;       /* outer Krylov iterations, summed over passes */
+  int inner_iters;       /* inner Krylov iterations, summed */
+  int refinements;       /* passes on the full residual */
+  int status;            /* stokes_status of the solve */
+  double rel_residual;   /* ||[F - A U + B^T P; g - B U]|| / ||[F; g]|| (FP64) */
+  double solve_ms;       /* wall time of the call (host clock) */
+} stokes_info;
+
+/* Fill *opt with the defaults: Method 1, C^Lambda, FP64, 2 V-cycles, degree 2
+ * Chebyshev, 8 mass steps, inner tolerance 1e-10 (the paper's Sec. 3.1). */
+void stokes_default_options(stokes_options* opt);
+
+/* Build every operator for one mesh and (mu, dt, gamma): element-coloured
+ * assembly on the device, multigrid hierarchy n -> n/2 -> ... , smoother
+ * spectra, coarse factors. `vertices` is a HOST array [(n+1)^3][3]; n >= 2.
+ * `stream` is a cudaStream_t (NULL = legacy default stream). mu, dt > 0,
+ * gamma >= 0. Returns STOKES_ERR_MESH if a jittered tetrahedron is inverted.
+ * On success *out owns all device memory of the solver. */
+stokes_status stokes_setup(int n, const double* vertices, double mu, double dt,
+                           double gamma, const stokes_options* opt,
+                           void* stream, stokes_ctx** out);
+
+/* Solve for (u, p). f: device [(2n+1)^3][3] nodal body force (the load is
+ * F = M_V f_h on interior rows). g: device [(n+1)^3] pressure load or NULL
+ * (zero); sum(g) must vanish (else STOKES_ERR_INCOMPATIBLE_RHS). tol: target
+ * for the true relative residual of the full system. u: device
+ * [(2n+1)^3][3] (boundary rows written as 0). p: device [(n+1)^3] with
+ * int p_h = 0. info may be NULL. */
+stokes_status stokes_solve(stokes_ctx* ctx, const double* f, const double* g,
+                           double tol, double* u, double* p, stokes_info* info);
+
+/* Same as stokes_solve with HOST arrays; the host<->device copies are part
+ * of the call. */
+stokes_status stokes_solve_host(stokes_ctx* ctx, const double* f, const double* g,
+                                double tol, double* u, double* p, stokes_info* info);
+
+/* Adjoint of stokes_solve for J(u, p): given dJ/du (device [(2n+1)^3][3],
+ * boundary rows ignored) and dJ/dp (device [(n+1)^3] or NULL), solve the
+ * transposed saddle system K^T [lu; lp] = [dJ/dU; dJ/dP] and return
+ * dJ/df (device [(2n+1)^3][3], = M_V^T lu spread to all nodes), dJ/dg
+ * (device [(n+1)^3] or NULL) and dJ/dmu (host scalar, = -lu^T E_V U for the
+ * (U, P) of the last stokes_solve). Requires a prior stokes_solve. */
+stokes_status stokes_adjoint(stokes_ctx* ctx, const double* dJdu, const double* dJdp,
+                             double tol, double* dJdf, double* dJdg, double* dJdmu,
+                             stokes_info* info);
+
+/* Release everything owned by ctx (NULL is accepted). */
+stokes_status stokes_destroy(stokes_ctx* ctx);
+
+/* Static description of a status code. */
+const char* stokes_status_string(int status);
+/* Message of the last failing call on this host thread ("" if none). */
+const char* stokes_last_error(void);
+
+/* ---- operator access: building blocks of the solve, for tests and tools ----
+ * Operators act on REDUCED vectors: velocity = interior P2 nodes
+ * [(2n-1)^3][3] (interleaved), pressure = [(n+1)^3]. x and y are device
+ * arrays of the operator's column / row length. `level` selects a multigrid
+ * level (0 = the mesh given to setup) where it applies, else must be 0. */
+typedef enum {
+  STOKES_OP_A = 0,            /* y = A x (strain form, 3x3 blocks)            */
+  STOKES_OP_A3 = 1,           /* y = A~_3 x per component (any level)         */
+  STOKES_OP_B = 2,            /* y = B x    (velocity -> pressure)            */
+  STOKES_OP_BT = 3,           /* y = B^T x  (pressure -> velocity)            */
+  STOKES_OP_MQ = 4,           /* y = M_Q x                                    */
+  STOKES_OP_LQ = 5,           /* y = L_Q x                                    */
+  STOKES_OP_KQ = 6,           /* y = (eps M_Q + L_Q) x  (any level)           */
+  STOKES_OP_LUMPED_INV = 7,   /* y = Lambda_V^{-1} x                          */
+  STOKES_OP_VCYCLE_A3 = 8,    /* y = vcycles V-cycles for A~_3 from 0 (level) */
+  STOKES_OP_VCYCLE_KQ = 9,    /* y = one V-cycle for eps M_Q + L_Q from 0     */
+  STOKES_OP_SCHUR_PREC = 10,  /* y = C x (C^Lambda or C^Delta per options)    */
+  STOKES_OP_SCHUR = 11,       /* y = B A^{-1} B^T x with the inner PCG        */
+  STOKES_OP_AGAMMA = 12,      /* y = A x + gamma mu B^T M_Q^{-1} B x           */
+  STOKES_OP_PROLONG_P2 = 13,  /* y(level) = P x(level+1), 3 components         */
+  STOKES_OP_RESTRICT_P2 = 14, /* y(level+1) = P^T x(level)                     */
+  STOKES_OP_PROLONG_P1 = 15,  /* y(level) = P x(level+1)                       */
+  STOKES_OP_LOAD = 16         /* y = M_V f on interior rows, x = nodal f (all) */
+} stokes_op;
+
+stokes_status stokes_apply(stokes_ctx* ctx, int op, int level, const double* x, double* y);
+
+/* Assembled matrices, for checks against an independent assembly. */
+typedef enum {
+  STOKES_MAT_A = 0,    /* BSR 3x3, interior P2 x interior P2                 */
+  STOKES_MAT_A3 = 1,   /* scalar, interior P2 (any level)                     */
+  STOKES_MAT_B = 2,    /* 1x3 blocks, P1 x interior P2                        */
+  STOKES_MAT_BT = 3,   /* 3x1 blocks, interior P2 x P1                        */
+  STOKES_MAT_MQ = 4, STOKES_MAT_LQ = 5,
+  STOKES_MAT_KQ = 6,   /* any level */
+  STOKES_MAT_LUMPED = 7/* diagonal Lambda_V per interior P2 node (rows=cols) */
+} stokes_matrix;
+
+/* dims = {rows, cols, nnz (blocks), block_rows, block_cols}. */
+stokes_status stokes_matrix_shape(stokes_ctx* ctx, int which, int level, int64_t dims[5]);
+/* Copy CSR arrays to HOST buffers sized from stokes_matrix_shape: rowptr
+ * [rows+1], colidx [nnz], vals [nnz*block_rows*block_cols] (row-major blocks).
+ * For STOKES_MAT_LUMPED only vals [rows] is written. */
+stokes_status stokes_matrix_export(stokes_ctx* ctx, int which, int level,
+                                   int32_t* rowptr, int32_t* colidx, double* vals);
+
+/* Problem sizes: {n, levels, interior P2 nodes, P1 nodes, all P2 nodes, dofs}. */
+stokes_status stokes_sizes(stokes_ctx* ctx, int64_t sizes[6]);
+
+/* Per-kernel timing (options.profile = 1): kernel ids are STOKES_KERNEL_*.
+ * Returns launches, summed CUDA-event milliseconds and algorithmic bytes
+ * (matrix read once, each vector read/written once) since the last reset. */
+typedef enum {
+  STOKES_KERNEL_SPMM_A3 = 0,      /* scalar CSR x 3 RHS (smoother/residual) */
+  STOKES_KERNEL_SPMV_A = 1,       /* BSR3 strain-form A                     */
+  STOKES_KERNEL_B = 2,            /* divergence B                           */
+  STOKES_KERNEL_BT = 3,           /* gradient B^T                           */
+  STOKES_KERNEL_SPMV_P1 = 4,      /* P1 CSR (M_Q, L_Q, eps M_Q + L_Q)       */
+  STOKES_KERNEL_TRANSFER = 5,     /* prolongation / restriction             */
+  STOKES_KERNEL_BLAS1 = 6,        /* dots, axpys, projections               */
+  STOKES_KERNEL_OTHER = 7,        /* load vectors, coarse solves, layouts   */
+  STOKES_KERNEL_COUNT = 8
+} stokes_kernel;
+stokes_status stokes_kernel_stats(stokes_ctx* ctx, int kernel, int64_t* launches,
+                                  double* total_ms, double* bytes);
+stokes_status stokes_kernel_stats_reset(stokes_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOKES_H */

@@ -1,0 +1,254 @@
+"""GB300-native generalized Stokes solver (P2-P1 Taylor-Hood on Kuhn meshes).
+
+Thin Python binding over the C ABI of ``include/stokes.h``: the functions here
+have the C names and only marshal arguments (PyTorch tensors provide device
+memory and streams). Every step of a solve runs in the CUDA library; importing
+this package without the compiled library raises.
+
+Method (Creff & Guermond, arXiv 2407.01783): A U - B^T P = F, B U = g with
+A = M_V/dt + mu E_V (optionally augmented Lagrangian), solved by Schur-complement
+CG with the Cahouet-Chabard preconditioner (Method 1) or by FGMRES with a
+block preconditioner on the coupled system (Method 2).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (KERNEL, MAT, METHOD_COUPLED, METHOD_SCHUR, OP, PRECISION_FP64,
+                   PRECISION_MIXED, SCHUR_PREC_LAPLACE, SCHUR_PREC_LUMPED, StokesInfo,
+                   StokesOptions)
+
+__all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "stokes_default_options",
+           "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_adjoint",
+           "stokes_destroy", "stokes_apply", "stokes_matrix_export", "stokes_sizes",
+           "stokes_kernel_stats", "stokes_kernel_stats_reset", "StokesSolve", "OP", "MAT",
+           "KERNEL", "METHOD_SCHUR", "METHOD_COUPLED", "SCHUR_PREC_LUMPED",
+           "SCHUR_PREC_LAPLACE", "PRECISION_FP64", "PRECISION_MIXED", "library_path"]
+
+_L = _lib.load()
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+class StokesError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _L.stokes_last_error().decode() or _L.stokes_status_string(status).decode()
+        super().__init__(f"{where}: {_lib.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str, allow=()):
+    if status != 0 and status not in allow:
+        raise StokesError(status, where)
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def stokes_default_options(**overrides) -> StokesOptions:
+    o = StokesOptions()
+    _L.stokes_default_options(C.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def stokes_setup(n: int, vertices, mu: float, dt: float, gamma: float = 0.0,
+                 options: StokesOptions | None = None, stream: torch.cuda.Stream | None = None):
+    """Build all operators on the current CUDA device; returns an opaque handle."""
+    V = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64))
+    if V.shape != ((n + 1) ** 3, 3):
+        raise ValueError(f"vertices must have shape {((n + 1) ** 3, 3)}")
+    if options is None:
+        options = stokes_default_options()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    h = C.c_void_p()
+    _check(_L.stokes_setup(n, _ptr(V), mu, dt, gamma, C.byref(options),
+                           C.c_void_p(s.cuda_stream), C.byref(h)), "stokes_setup")
+    return h
+
+
+def stokes_solve(ctx, f: torch.Tensor, g: torch.Tensor | None, tol: float, u: torch.Tensor,
+                 p: torch.Tensor, allow_not_converged: bool = False) -> StokesInfo:
+    info = StokesInfo()
+    _check(_L.stokes_solve(ctx, _ptr(f), _ptr(g), tol, _ptr(u), _ptr(p), C.byref(info)),
+           "stokes_solve", allow=(-4,) if allow_not_converged else ())
+    return info
+
+
+def stokes_solve_host(ctx, f: np.ndarray, g: np.ndarray | None, tol: float, u: np.ndarray,
+                      p: np.ndarray) -> StokesInfo:
+    info = StokesInfo()
+    _check(_L.stokes_solve_host(ctx, _ptr(f), _ptr(g), tol, _ptr(u), _ptr(p), C.byref(info)),
+           "stokes_solve_host")
+    return info
+
+
+def stokes_adjoint(ctx, dJdu, dJdp, tol, dJdf, dJdg=None):
+    info = StokesInfo()
+    dmu = C.c_double(0.0)
+    _check(_L.stokes_adjoint(ctx, _ptr(dJdu), _ptr(dJdp), tol, _ptr(dJdf), _ptr(dJdg),
+                             C.byref(dmu), C.byref(info)), "stokes_adjoint")
+    return dmu.value, info
+
+
+def stokes_destroy(ctx):
+    if ctx:
+        _L.stokes_destroy(ctx)
+
+
+def stokes_apply(ctx, op: int, x: torch.Tensor, y: torch.Tensor, level: int = 0):
+    _check(_L.stokes_apply(ctx, op, level, _ptr(x), _ptr(y)), "stokes_apply")
+    return y
+
+
+def stokes_sizes(ctx) -> dict:
+    s = (C.c_int64 * 6)()
+    _check(_L.stokes_sizes(ctx, s), "stokes_sizes")
+    return dict(n=s[0], levels=s[1], n_inner=s[2], n_p1=s[3], n_p2=s[4], dofs=s[5])
+
+
+def stokes_matrix_export(ctx, which: int, level: int = 0):
+    """(rowptr, colidx, vals[nnz, br, bc], (rows, cols)) of an assembled matrix."""
+    d = (C.c_int64 * 5)()
+    _check(_L.stokes_matrix_shape(ctx, which, level, d), "stokes_matrix_shape")
+    rows, cols, nnz, br, bc = (int(x) for x in d)
+    if which == MAT["LUMPED"]:
+        vals = np.zeros(rows)
+        _check(_L.stokes_matrix_export(ctx, which, level, None, None, _ptr(vals)),
+               "stokes_matrix_export")
+        return None, None, vals, (rows, cols)
+    rp = np.zeros(rows + 1, np.int32)
+    ci = np.zeros(max(nnz, 1), np.int32)
+    vals = np.zeros(max(nnz, 1) * br * bc)
+    _check(_L.stokes_matrix_export(ctx, which, level, _ptr(rp), _ptr(ci), _ptr(vals)),
+           "stokes_matrix_export")
+    return rp, ci[:nnz], vals[: nnz * br * bc].reshape(nnz, br, bc), (rows, cols)
+
+
+def stokes_kernel_stats(ctx, kernel: int):
+    n = C.c_int64(0)
+    ms = C.c_double(0)
+    by = C.c_double(0)
+    _check(_L.stokes_kernel_stats(ctx, kernel, C.byref(n), C.byref(ms), C.byref(by)),
+           "stokes_kernel_stats")
+    return int(n.value), float(ms.value), float(by.value)
+
+
+def stokes_kernel_stats_reset(ctx):
+    _check(_L.stokes_kernel_stats_reset(ctx), "stokes_kernel_stats_reset")
+
+
+class Stokes:
+    """Owning wrapper: one mesh, one (mu, dt, gamma), reusable across solves."""
+
+    def __init__(self, n: int, vertices, mu: float, dt: float, gamma: float = 0.0,
+                 options: StokesOptions | None = None, device: str | torch.device = "cuda"):
+        self.n, self.mu, self.dt, self.gamma = n, mu, dt, gamma
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.options = options if options is not None else stokes_default_options()
+            self.ctx = stokes_setup(n, vertices, mu, dt, gamma, self.options)
+        self.sizes = stokes_sizes(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            stokes_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_p2(self):
+        return self.sizes["n_p2"]
+
+    @property
+    def n_p1(self):
+        return self.sizes["n_p1"]
+
+    def solve(self, f: torch.Tensor, g: torch.Tensor | None = None, tol: float = 1e-8,
+              out=None, allow_not_converged=False):
+        f = f.to(self.device, torch.float64).contiguous().reshape(self.n_p2, 3)
+        if g is not None:
+            g = g.to(self.device, torch.float64).contiguous()
+        if out is None:
+            u = torch.empty_like(f)
+            p = torch.empty(self.n_p1, dtype=torch.float64, device=self.device)
+        else:
+            u, p = out
+        info = stokes_solve(self.ctx, f, g, tol, u, p, allow_not_converged)
+        return u, p, info
+
+    def solve_host(self, f: np.ndarray, g: np.ndarray | None = None, tol: float = 1e-8):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.n_p2, 3)
+        u = np.empty_like(f)
+        p = np.empty(self.n_p1)
+        if g is not None:
+            g = np.ascontiguousarray(g, dtype=np.float64)
+        info = stokes_solve_host(self.ctx, f, g, tol, u, p)
+        return u, p, info
+
+    def adjoint(self, dJdu: torch.Tensor, dJdp: torch.Tensor | None = None, tol: float = 1e-10):
+        dJdu = dJdu.to(self.device, torch.float64).contiguous()
+        if dJdp is not None:
+            dJdp = dJdp.to(self.device, torch.float64).contiguous()
+        dJdf = torch.empty(self.n_p2, 3, dtype=torch.float64, device=self.device)
+        dJdg = torch.empty(self.n_p1, dtype=torch.float64, device=self.device)
+        dmu, info = stokes_adjoint(self.ctx, dJdu, dJdp, tol, dJdf, dJdg)
+        return dJdf, dJdg, dmu, info
+
+    def apply(self, op: str, x: torch.Tensor, out_len: int, level: int = 0) -> torch.Tensor:
+        y = torch.zeros(out_len, dtype=torch.float64, device=self.device)
+        stokes_apply(self.ctx, OP[op], x.contiguous(), y, level)
+        return y
+
+    def matrix(self, which: str, level: int = 0):
+        return stokes_matrix_export(self.ctx, MAT[which], level)
+
+    def kernel_stats(self, kernel: str):
+        return stokes_kernel_stats(self.ctx, KERNEL[kernel])
+
+
+class StokesSolve(torch.autograd.Function):
+    """u, p = StokesSolve.apply(solver, f, mu_tensor, tol): forward solve, and a
+    hand-written adjoint for backward giving dJ/df and dJ/dmu (the solver's mu is
+    fixed at setup; mu_tensor only carries the gradient)."""
+
+    @staticmethod
+    def forward(ctx, solver: Stokes, f: torch.Tensor, mu: torch.Tensor, tol: float = 1e-10):
+        u, p, info = solver.solve(f, None, tol)
+        ctx.solver = solver
+        ctx.tol = tol
+        return u, p
+
+    @staticmethod
+    def backward(ctx, gu, gp):
+        solver = ctx.solver
+        gu = torch.zeros(solver.n_p2, 3, dtype=torch.float64, device=solver.device) if gu is None else gu
+        dJdf, dJdg, dmu, info = solver.adjoint(gu, gp, ctx.tol)
+        return None, dJdf, torch.tensor(dmu, dtype=torch.float64, device=solver.device), None

@@ -1,0 +1,273 @@
+// Vector kernels for the Krylov solvers: multi-dot products accumulated in
+// FP64 with a fixed reduction order (per-block partials, then the last block
+// to finish sums them in block order), and fused axpy-type updates whose
+// coefficients are read from device-resident scalars so that the host never
+// waits for a dot product it does not need to see.
+#include <cmath>
+
+#include "internal.h"
+
+namespace sk {
+
+__device__ __forceinline__ double coef_value(const Coef& k) {
+  double v = k.c;
+  if (k.num) v += k.s * (*k.num) / (k.den ? *k.den : 1.0);
+  return v;
+}
+
+template <class T> struct DotArgs {
+  const T* x[kMaxDots];
+  const T* y[kMaxDots];
+  int k;
+  size_t n;
+  double* partial;
+  unsigned* counter;
+  double* out;
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dots(DotArgs<T> a) {
+  double s[kMaxDots];
+#pragma unroll
+  for (int j = 0; j < kMaxDots; ++j) s[j] = 0.0;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+#pragma unroll
+    for (int j = 0; j < kMaxDots; ++j)
+      if (j < a.k) s[j] += (double)a.x[j][i] * (a.y[j] ? (double)a.y[j][i] : 1.0);
+  }
+  __shared__ double sh[kMaxDots][8];
+  __shared__ bool last;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kMaxDots; ++j) {
+    double v = s[j];
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[j][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxDots) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+    a.partial[threadIdx.x * gridDim.x + blockIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  // the last block: fixed-order sum of the partials
+  for (int j = 0; j < a.k; ++j) {
+    double v = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(&a.partial[j * gridDim.x + b]);
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[0][wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[0][w];
+      a.out[j] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+template <class T>
+void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const T* const* y, size_t n, double* out) {
+  SK_REQUIRE(k >= 1 && k <= kMaxDots, STOKES_ERR_ARG, "dots: bad count");
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, 0.0 + (double)sizeof(T) * n * (2.0 * k));
+  DotArgs<T> a{};
+  for (int j = 0; j < k; ++j) a.x[j] = x[j], a.y[j] = y ? y[j] : nullptr;
+  a.k = k;
+  a.n = n;
+  a.partial = ds.partial;
+  a.counter = ds.counter;
+  a.out = out;
+  int grid = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, cdiv((long long)n, 256)));
+  k_dots<T><<<grid, 256, 0, ex.s>>>(a);
+  SK_CHECK_LAUNCH();
+}
+
+#define SK_GRID(n) cdiv((long long)(n), 256), 256, 0, ex.s
+#define SK_IDX                                              \
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; \
+  if (i >= n) return;
+
+template <class T>
+__global__ void k_axpby(size_t n, Coef a, const T* __restrict__ x, Coef b, T* __restrict__ y) {
+  SK_IDX;
+  T av = (T)coef_value(a), bv = (T)coef_value(b);
+  y[i] = av * x[i] + (bv == T(0) ? T(0) : bv * y[i]);
+}
+template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 3);
+  k_axpby<T><<<SK_GRID(n)>>>(n, a, x, b, y);
+  SK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_cg_update(size_t n, Coef a, const T* __restrict__ d, T* __restrict__ x, const T* __restrict__ q,
+                            T* __restrict__ r, int* flag) {
+  SK_IDX;
+  double av = coef_value(a);
+  if (i == 0 && a.den && !(*a.den > 0.0)) atomicOr(flag, 1);  // p^T A p <= 0: breakdown
+  x[i] += (T)av * d[i];
+  if (r) r[i] -= (T)av * q[i];
+}
+static int* g_flag = nullptr;  // set by the context before solves
+void set_breakdown_flag(int* f) { g_flag = f; }
+template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * (r ? 6 : 3));
+  k_cg_update<T><<<SK_GRID(n)>>>(n, a, d, x, q, r, g_flag);
+  SK_CHECK_LAUNCH();
+}
+
+template <class T> __global__ void k_scale_copy(size_t n, Coef a, const T* __restrict__ x, T* __restrict__ y) {
+  SK_IDX;
+  y[i] = (T)coef_value(a) * x[i];
+}
+template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x, T* y) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 2);
+  k_scale_copy<T><<<SK_GRID(n)>>>(n, a, x, y);
+  SK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_lincomb2(size_t n, T c1, const T* __restrict__ x1, T c2, const T* __restrict__ x2, T* __restrict__ y) {
+  SK_IDX;
+  y[i] = c1 * x1[i] + c2 * x2[i];
+}
+template <class T> void lincomb2(const Exec& ex, size_t n, double c1, const T* x1, double c2, const T* x2, T* y) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 3);
+  k_lincomb2<T><<<SK_GRID(n)>>>(n, (T)c1, x1, (T)c2, x2, y);
+  SK_CHECK_LAUNCH();
+}
+
+template <class T> __global__ void k_sub_ratio(size_t n, const double* num, const double* den, double scale, T* x) {
+  SK_IDX;
+  x[i] -= (T)(scale * (*num) / (den ? *den : 1.0));
+}
+template <class T> void sub_mean(const Exec& ex, size_t n, const double* sum, double count, T* r) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 2);
+  k_sub_ratio<T><<<SK_GRID(n)>>>(n, sum, nullptr, 1.0 / count, r);
+  SK_CHECK_LAUNCH();
+}
+template <class T> void sub_ratio(const Exec& ex, size_t n, const double* num, const double* den, T* x) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 2);
+  k_sub_ratio<T><<<SK_GRID(n)>>>(n, num, den, 1.0, x);
+  SK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_cheb_first(size_t n, int nr, const T* __restrict__ dinv, const T* __restrict__ b, T c,
+                             T* __restrict__ d, T* __restrict__ x) {
+  SK_IDX;
+  T v = c * dinv[i / nr] * b[i];
+  d[i] = v;
+  x[i] = v;
+}
+template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* dinv, const T* b, double c, T* d, T* x) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * (n * 3 + n / nr));
+  k_cheb_first<T><<<SK_GRID(n)>>>(n, nr, dinv, b, (T)c, d, x);
+  SK_CHECK_LAUNCH();
+}
+
+template <class S, class D> __global__ void k_convert(size_t n, const S* __restrict__ x, D* __restrict__ y) {
+  SK_IDX;
+  y[i] = (D)x[i];
+}
+template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D* y) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)(sizeof(S) + sizeof(D)) * n);
+  k_convert<S, D><<<SK_GRID(n)>>>(n, x, y);
+  SK_CHECK_LAUNCH();
+}
+template <class S, class D> __global__ void k_add_convert(size_t n, const S* __restrict__ x, D* __restrict__ y) {
+  SK_IDX;
+  y[i] += (D)x[i];
+}
+template <class S, class D> void add_convert(const Exec& ex, size_t n, const S* x, D* y) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)(sizeof(S) + 2 * sizeof(D)) * n);
+  k_add_convert<S, D><<<SK_GRID(n)>>>(n, x, y);
+  SK_CHECK_LAUNCH();
+}
+
+// reduced interior velocity [(2n-1)^3][3] <-> all-node field [(2n+1)^3][3]
+__global__ void k_expand(int n, const double* __restrict__ ured, double* __restrict__ uall) {
+  int N = 2 * n + 1, m = 2 * n - 1;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)N * N * N;
+  if (i >= tot) return;
+  int qx = (int)(i % N), qy = (int)((i / N) % N), qz = (int)(i / ((size_t)N * N));
+  bool in = qx > 0 && qx < N - 1 && qy > 0 && qy < N - 1 && qz > 0 && qz < N - 1;
+  size_t r = in ? (size_t)(qx - 1) + (size_t)m * ((qy - 1) + (size_t)m * (qz - 1)) : 0;
+  for (int c = 0; c < 3; ++c) uall[3 * i + c] = in ? ured[3 * r + c] : 0.0;
+}
+void expand_velocity(const Exec& ex, int n, const double* ured, double* uall) {
+  size_t tot = (size_t)(2 * n + 1) * (2 * n + 1) * (2 * n + 1);
+  ProfScope ps(ex, STOKES_KERNEL_OTHER, 48.0 * tot);
+  k_expand<<<SK_GRID(tot)>>>(n, ured, uall);
+  SK_CHECK_LAUNCH();
+}
+__global__ void k_restrict_vel(int n, const double* __restrict__ uall, double* __restrict__ ured) {
+  int N = 2 * n + 1, m = 2 * n - 1;
+  size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)m * m * m;
+  if (r >= tot) return;
+  int ix = (int)(r % m) + 1, iy = (int)((r / m) % m) + 1, iz = (int)(r / ((size_t)m * m)) + 1;
+  size_t g = (size_t)ix + (size_t)N * (iy + (size_t)N * iz);
+  for (int c = 0; c < 3; ++c) ured[3 * r + c] = uall[3 * g + c];
+}
+void restrict_velocity(const Exec& ex, int n, const double* uall, double* ured) {
+  size_t tot = (size_t)(2 * n - 1) * (2 * n - 1) * (2 * n - 1);
+  ProfScope ps(ex, STOKES_KERNEL_OTHER, 48.0 * tot);
+  k_restrict_vel<<<SK_GRID(tot)>>>(n, uall, ured);
+  SK_CHECK_LAUNCH();
+}
+
+__global__ void k_nonfinite(size_t n, const double* __restrict__ x, int* flag) {
+  SK_IDX;
+  if (!isfinite(x[i])) atomicOr(flag, 2);
+}
+void count_nonfinite(const Exec& ex, size_t n, const double* x, int* flag) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_OTHER, 8.0 * n);
+  k_nonfinite<<<SK_GRID(n)>>>(n, x, flag);
+  SK_CHECK_LAUNCH();
+}
+
+__global__ void k_scalar_sub(double* out, const double* a, const double* b) { *out = *a - *b; }
+void scalar_sub(const Exec& ex, double* out, const double* a, const double* b) {
+  ProfScope ps(ex, STOKES_KERNEL_OTHER, 24.0);
+  k_scalar_sub<<<1, 1, 0, ex.s>>>(out, a, b);
+  SK_CHECK_LAUNCH();
+}
+
+#define SK_INST1(T)                                                                                     \
+  template void dots<T>(const Exec&, const DotScratch&, int, const T* const*, const T* const*, size_t, \
+                        double*);                                                                       \
+  template void axpby<T>(const Exec&, size_t, Coef, const T*, Coef, T*);                               \
+  template void cg_update<T>(const Exec&, size_t, Coef, const T*, T*, const T*, T*);                   \
+  template void scale_copy<T>(const Exec&, size_t, Coef, const T*, T*);                                \
+  template void lincomb2<T>(const Exec&, size_t, double, const T*, double, const T*, T*);              \
+  template void sub_mean<T>(const Exec&, size_t, const double*, double, T*);                           \
+  template void sub_ratio<T>(const Exec&, size_t, const double*, const double*, T*);                   \
+  template void cheb_first<T>(const Exec&, size_t, int, const T*, const T*, double, T*, T*);
+SK_INST1(float)
+SK_INST1(double)
+template void convert<double, float>(const Exec&, size_t, const double*, float*);
+template void convert<float, double>(const Exec&, size_t, const float*, double*);
+template void convert<double, double>(const Exec&, size_t, const double*, double*);
+template void add_convert<float, double>(const Exec&, size_t, const float*, double*);
+template void add_convert<double, double>(const Exec&, size_t, const double*, double*);
+
+}  // namespace sk

@@ -1,0 +1,303 @@
+// Internal declarations of the GB300 generalized-Stokes library.
+// Host orchestration (solver.cu, capi.cu) talks to the kernels (assembly.cu,
+// sparse.cu, blas1.cu) only through the launch wrappers declared here.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "../../include/stokes.h"
+
+namespace sk {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+  int status;
+  Error(int s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define SK_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      throw ::sk::Error(e_ == cudaErrorMemoryAllocation ? STOKES_ERR_OOM           \
+                                                        : STOKES_ERR_CUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+#define SK_CHECK_LAUNCH() SK_CUDA(cudaGetLastError())
+#define SK_REQUIRE(cond, st, msg) \
+  do {                            \
+    if (!(cond)) throw ::sk::Error((st), (msg)); \
+  } while (0)
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// profiling: CUDA events around launches of one kernel class
+// ---------------------------------------------------------------------------
+struct Prof {
+  bool on = false;
+  struct Rec {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    double bytes = 0;
+    int64_t launches = 0;
+  } rec[STOKES_KERNEL_COUNT];
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void reset();
+  ~Prof();
+};
+
+struct Exec {
+  cudaStream_t s = nullptr;
+  Prof* prof = nullptr;
+};
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+  Exec ex;
+  int kind;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(const Exec& e, int k, double bytes);
+  ~ProfScope();
+};
+
+// ---------------------------------------------------------------------------
+// sparse matrices: CSR over (possibly) small dense blocks, values stored as
+// br*bc planes of nnz entries each (plane j at v + j*nnz) so that consecutive
+// lanes read consecutive addresses.
+// ---------------------------------------------------------------------------
+struct Csr {
+  int rows = 0, cols = 0;
+  long long nnz = 0;
+  int br = 1, bc = 1;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  int group = 8;  // threads per row
+  template <class T> T* v() const;
+  double bytes(int elem) const {  // algorithmic bytes of one product (matrix only)
+    return (double)nnz * (4.0 + elem * br * bc) + 4.0 * (rows + 1);
+  }
+};
+template <> inline double* Csr::v<double>() const { return v64; }
+template <> inline float* Csr::v<float>() const { return v32; }
+
+// Device allocations owned by a context.
+struct Arena {
+  std::vector<void*> ptrs;
+  void* raw(size_t bytes);
+  template <class T> T* alloc(size_t n) { return (T*)raw(sizeof(T) * (n ? n : 1)); }
+  void free_all();
+};
+
+// Reusable device vectors keyed by (element size, length): after the first
+// solve no further allocation happens.
+struct VecPool {
+  Arena* arena = nullptr;
+  std::unordered_map<uint64_t, std::vector<void*>> free_;
+  void* get(size_t elems, int esz);
+  void put(void* p, size_t elems, int esz);
+};
+
+template <class T> struct Tmp {
+  VecPool* pool;
+  size_t n;
+  T* p;
+  Tmp(VecPool& vp, size_t n_) : pool(&vp), n(n_), p((T*)vp.get(n_, sizeof(T))) {}
+  ~Tmp() { pool->put(p, n, sizeof(T)); }
+  Tmp(const Tmp&) = delete;
+  Tmp& operator=(const Tmp&) = delete;
+  operator T*() const { return p; }
+};
+
+// Device-resident FP64 scalars used by Krylov kernels (no host round trip).
+struct Scalars {
+  double* d = nullptr;     // device slots
+  double* h = nullptr;     // pinned host mirror
+  int cap = 0, top = 0;
+  int take(int k) {
+    SK_REQUIRE(top + k <= cap, STOKES_ERR_ARG, "scalar slot pool exhausted");
+    int s = top;
+    top += k;
+    return s;
+  }
+  void give(int k) { top -= k; }
+};
+
+// Coefficient read on the device: value = c + s * (*num / *den); null num -> 0
+// contribution, null den -> 1.
+struct Coef {
+  double c = 0, s = 0;
+  const double* num = nullptr;
+  const double* den = nullptr;
+  static Coef constant(double v) { Coef k; k.c = v; return k; }
+  static Coef ratio(const double* num, const double* den, double s = 1.0) {
+    Coef k; k.s = s; k.num = num; k.den = den; return k;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// multigrid levels
+// ---------------------------------------------------------------------------
+struct Level {
+  int n = 0;
+  int nvi = 0;  // interior P2 nodes (2n-1)^3
+  int np = 0;   // P1 nodes (n+1)^3
+  double* X = nullptr;  // vertex coordinates of this level
+  Csr A3, KQ;           // A~_3 (scalar) and eps M_Q + L_Q
+  double *A3_dinv64 = nullptr, *KQ_dinv64 = nullptr;
+  float *A3_dinv32 = nullptr, *KQ_dinv32 = nullptr;
+  double A3_lmax = 0, KQ_lmax = 0;  // lambda_max(D^{-1} A) estimates
+  Csr P2, R2, P1, R1;               // transfers to/from level+1 (P: this <- coarse)
+  // coarsest level: dense inverses (row-major)
+  double *A3_cinv64 = nullptr, *KQ_cinv64 = nullptr;
+  float *A3_cinv32 = nullptr, *KQ_cinv32 = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// launch wrappers (assembly.cu)
+// ---------------------------------------------------------------------------
+enum PatternKind { PAT_P2P2 = 0, PAT_P1P1 = 1, PAT_P1P2 = 2, PAT_P2P1 = 3 };
+struct StencilTables;  // device stencil offsets
+StencilTables* stencils_create(Arena& ar);
+void build_pattern(const Exec& ex, Arena& ar, const StencilTables* st, PatternKind kind,
+                   int n, Csr& m);
+
+struct AssemblyOut {
+  double* a3 = nullptr;     // scalar A~_3 on the P2P2 pattern
+  double* abs = nullptr;    // BSR3 A (9 planes) on the P2P2 pattern
+  double* mq = nullptr;     // P1 mass on the P1P1 pattern
+  double* lq = nullptr;     // P1 Laplacian
+  double* kq = nullptr;     // eps M_Q + L_Q
+  double* b = nullptr;      // B (3 planes) on the P1P2 pattern
+  double* bt = nullptr;     // B^T (3 planes) on the P2P1 pattern
+  double* lumped = nullptr; // Lambda_V per interior node
+};
+// Returns the number of inverted/degenerate tetrahedra.
+long long assemble(const Exec& ex, int n, const double* X, double mu, double dt,
+                   double eps, const Csr& p2, const Csr& p1, const Csr* b, const Csr* bt,
+                   const AssemblyOut& out, int* d_bad);
+void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat,
+                   const double* f_all, double* F);
+// out = M_V^T lu on all P2 nodes (lu on interior nodes, 3 components)
+void assemble_load_transpose(const Exec& ex, int n, const double* X, const double* lu, double* out);
+void build_transfer_p2(const Exec& ex, Arena& ar, int nf, int nc, Csr& P, Csr& R);
+void build_transfer_p1(const Exec& ex, Arena& ar, int nf, int nc, Csr& P, Csr& R);
+void diag_inverse(const Exec& ex, const Csr& m, double* dinv);
+void to_f32(const Exec& ex, const double* src, float* dst, size_t n);
+void subsample_vertices(int n, const double* Xf_host, double* Xc_host);
+
+// ---------------------------------------------------------------------------
+// sparse products (sparse.cu); T = vector/matrix precision
+// ---------------------------------------------------------------------------
+// y = A x for scalar CSR with NR interleaved right-hand sides.
+template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind);
+// y = b - A x
+template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind);
+// y += A x
+template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind);
+// Chebyshev step: r = b - A xin; d = c1 d + c2 dinv r; xout = xin + d.
+template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin,
+                                  T* d, T* xout, const T* dinv, double c1, double c2);
+// BSR3 strain-form A: y = A x or y = b - A x (b may be null).
+template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b);
+// B (1x3 blocks): y = B x;  B^T (3x1 blocks): y = B^T x, optionally scaled per row
+// (y_i = s_i * (B^T x)_i) and / or subtracted from b (y = b - ...) or added into y.
+template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha);
+template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* scale,
+                                 const T* b, double alpha);
+template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y);
+void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
+
+// ---------------------------------------------------------------------------
+// BLAS-1 (blas1.cu). Dot products accumulate in FP64 and reduce in a fixed
+// order (deterministic).
+// ---------------------------------------------------------------------------
+struct DotScratch {
+  double* partial = nullptr;   // [kMaxDots][kMaxBlocks]
+  unsigned* counter = nullptr;
+};
+constexpr int kMaxDots = 4;
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+// out[i] = sum_j x_i[j] * y_i[j] for i < k (y_i == nullptr means all ones).
+template <class T> void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x,
+                             const T* const* y, size_t n, double* out);
+template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y);
+// x += a d; r -= a q   (a from device scalars)
+template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r);
+// y = a x  (a may be a device ratio)
+template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x, T* y);
+// y = c1*x1 + c2*x2 (elementwise, constants)
+template <class T> void lincomb2(const Exec& ex, size_t n, double c1, const T* x1, double c2, const T* x2, T* y);
+// r -= (*sum / count) (subtract the mean, sum computed beforehand on device)
+template <class T> void sub_mean(const Exec& ex, size_t n, const double* sum, double count, T* r);
+// x -= (*s1 / *s2) * 1
+template <class T> void sub_ratio(const Exec& ex, size_t n, const double* num, const double* den, T* x);
+// elementwise y = dinv * x * c (first Chebyshev step from zero: d = x = c D^{-1} b)
+template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* dinv, const T* b,
+                                   double c, T* d, T* x);
+template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D* y);
+template <class S, class D> void add_convert(const Exec& ex, size_t n, const S* x, D* y);
+void expand_velocity(const Exec& ex, int n, const double* ured, double* uall);
+void restrict_velocity(const Exec& ex, int n, const double* uall, double* ured);
+void count_nonfinite(const Exec& ex, size_t n, const double* x, int* flag);
+
+}  // namespace sk
+
+// ---------------------------------------------------------------------------
+// the context (defined in capi.cu, used by solver.cu)
+// ---------------------------------------------------------------------------
+struct stokes_ctx {
+  int n = 0;
+  double mu = 0, dt = 0, gamma = 0;
+  stokes_options opt{};
+  sk::Exec ex;
+  sk::Prof prof;
+  sk::Arena arena;
+  sk::VecPool pool;
+  sk::Scalars sc;
+  sk::DotScratch ds;
+  int* d_flag = nullptr;
+  std::vector<sk::Level> lv;
+  sk::Csr A, B, Bt, MQ, LQ;  // fine level (P2P2 BSR3, P1P2, P2P1, P1P1, P1P1)
+  double* lumped = nullptr;  // Lambda_V per interior node
+  double *lumped_inv64 = nullptr;
+  float* lumped_inv32 = nullptr;
+  double* MQ_dinv64 = nullptr;
+  float* MQ_dinv32 = nullptr;
+  double* MQ1 = nullptr;     // M_Q 1
+  double MQ1_sum = 0;
+  bool mixed = false;
+  // last forward solution (reduced) for the adjoint
+  double* U_last = nullptr;
+  double* P_last = nullptr;
+  bool have_solution = false;
+  // host staging for *_host calls
+  double *f_dev = nullptr, *g_dev = nullptr, *u_dev = nullptr, *p_dev = nullptr;
+  cudaEvent_t ev_read = nullptr;  // host reads of device scalars
+  // counters
+  int outer_iters = 0, inner_iters = 0, schur_inner_iters = 0;
+  bool outer_capped = false, inner_capped = false;
+};
+
+namespace sk {
+void setup_context(stokes_ctx* c, int n, const double* Xhost);
+int solve_context(stokes_ctx* c, const double* f, const double* g, double tol, double* u,
+                  double* p, stokes_info* info);
+int adjoint_context(stokes_ctx* c, const double* dJdu, const double* dJdp, double tol,
+                    double* dJdf, double* dJdg, double* dJdmu, stokes_info* info);
+void apply_operator(stokes_ctx* c, int op, int level, const double* x, double* y);
+double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps, uint64_t seed);
+void set_breakdown_flag(int* f);
+void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
+}  // namespace sk

@@ -1,0 +1,820 @@
+// Solver orchestration on one GPU stream: Chebyshev-Jacobi smoothing,
+// geometric V-cycles, preconditioned CG, the Cahouet-Chabard Schur
+// preconditioner, Method 1 (flexible CG on the pressure Schur complement,
+// Sec. 2.3) and Method 2 (FGMRES on the coupled system with the block
+// preconditioner of Eq. inexact_factorization_of_Alambda, Sec. 2.4), wrapped in
+// defect correction on the full FP64 residual of Eq. Saddle_point_A_BT_B.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace sk {
+
+void set_breakdown_flag(int* f);
+void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
+
+// Smoother interval [kChebLow, kChebHigh] x (Lanczos estimate of lambda_max(D^{-1}A)).
+constexpr double kChebLow = 0.1;
+constexpr double kChebHigh = 1.1;
+// sigma(D^{-1} M_Q) lies in [1/2, 5/2] for P1 on tetrahedra (element matrix
+// D_K^{-1} M_K = (I + 1 1^T)/2 has eigenvalues 1/2 and 5/2; Wathen 1987).
+constexpr double kMassLow = 0.5;
+constexpr double kMassHigh = 2.5;
+
+template <class T> static inline const T* pick(const double* a, const float* b);
+template <> inline const double* pick<double>(const double* a, const float*) { return a; }
+template <> inline const float* pick<float>(const double*, const float* b) { return b; }
+
+// ---------------------------------------------------------------------------
+// host reads of device scalars
+// ---------------------------------------------------------------------------
+static double read_now(stokes_ctx& c, const double* d, int slot) {
+  SK_CUDA(cudaMemcpyAsync(c.sc.h + slot, d, sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  return c.sc.h[slot];
+}
+static void read_issue(stokes_ctx& c, const double* d, int slot) {
+  SK_CUDA(cudaMemcpyAsync(c.sc.h + slot, d, sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaEventRecord(c.ev_read, c.ex.s));
+}
+static double read_wait(stokes_ctx& c, int slot) {
+  SK_CUDA(cudaEventSynchronize(c.ev_read));
+  return c.sc.h[slot];
+}
+
+template <class T> static void dot1(stokes_ctx& c, const T* x, const T* y, size_t n, double* out) {
+  const T* xs[1] = {x};
+  const T* ys[1] = {y};
+  dots<T>(c.ex, c.ds, 1, xs, ys, n, out);
+}
+template <class T> static void copy(stokes_ctx& c, T* dst, const T* src, size_t n) {
+  SK_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, c.ex.s));
+}
+template <class T> static void zero(stokes_ctx& c, T* p, size_t n) {
+  SK_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), c.ex.s));
+}
+// r <- r - mean(r) (Euclidean complement of the constants: pressure residuals
+// live there because B^T 1 = 0)
+template <class T> static void project_mean(stokes_ctx& c, T* r, size_t n) {
+  int s = c.sc.take(1);
+  dot1<T>(c, r, (const T*)nullptr, n, c.sc.d + s);
+  sub_mean<T>(c.ex, n, c.sc.d + s, (double)n, r);
+  c.sc.give(1);
+}
+
+static size_t nvel(const stokes_ctx& c) { return 3 * (size_t)c.lv[0].nvi; }
+static size_t npres(const stokes_ctx& c) { return (size_t)c.lv[0].np; }
+
+// ---------------------------------------------------------------------------
+// Chebyshev semi-iteration for D^{-1} M on [lmin, lmax] (Saad, Alg. 12.1)
+// ---------------------------------------------------------------------------
+template <class T>
+static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double lmin, double lmax, int steps,
+                     const T* b, T* x, bool xzero) {
+  size_t len = (size_t)M.rows * nr;
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta, rho = 1.0 / sigma;
+  Tmp<T> d(c.pool, len), xt(c.pool, len);
+  T* xa = x;
+  T* xb = xt;
+  if (xzero) {
+    cheb_first<T>(c.ex, len, nr, dinv, b, 1.0 / theta, d, xa);
+  } else {
+    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, 0.0, 1.0 / theta);
+    std::swap(xa, xb);
+  }
+  for (int k = 1; k < steps; ++k) {
+    double rn = 1.0 / (2.0 * sigma - rho);
+    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, rn * rho, 2.0 * rn / delta);
+    std::swap(xa, xb);
+    rho = rn;
+  }
+  if (xa != x) copy<T>(c, x, xa, len);
+}
+
+// M_Q^{-1} b by Chebyshev-Jacobi on the exact Wathen interval
+template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int steps) {
+  cheb_run<T>(c, c.MQ, 1, pick<T>(c.MQ_dinv64, c.MQ_dinv32), kMassLow, kMassHigh, std::max(1, steps), b, x, true);
+}
+
+// ---------------------------------------------------------------------------
+// geometric V-cycle; which = 0: A~_3 on 3 interleaved components, 1: eps M_Q + L_Q
+// ---------------------------------------------------------------------------
+template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero) {
+  Level& L = c.lv[l];
+  const int nr = which ? 1 : 3;
+  const Csr& M = which ? L.KQ : L.A3;
+  size_t len = (size_t)M.rows * nr;
+  if (l + 1 == (int)c.lv.size()) {
+    const T* Minv = which ? pick<T>(L.KQ_cinv64, L.KQ_cinv32) : pick<T>(L.A3_cinv64, L.A3_cinv32);
+    dense_apply<T>(c.ex, Minv, M.rows, nr, b, x);
+    return;
+  }
+  const T* dinv = which ? pick<T>(L.KQ_dinv64, L.KQ_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32);
+  double lmax = kChebHigh * (which ? L.KQ_lmax : L.A3_lmax), lmin = kChebLow * (which ? L.KQ_lmax : L.A3_lmax);
+  int deg = std::max(1, c.opt.cheb_degree);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero);
+  Level& Lc = c.lv[l + 1];
+  const Csr& Mc = which ? Lc.KQ : Lc.A3;
+  size_t lenc = (size_t)Mc.rows * nr;
+  {
+    Tmp<T> r(c.pool, len);
+    spmv_resid<T>(c.ex, M, nr, b, x, r, nr == 3 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMV_P1);
+    Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);
+    spmv_store<T>(c.ex, which ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER);
+    vcycle<T>(c, which, l + 1, bc, xc, true);
+    spmv_add<T>(c.ex, which ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER);
+  }
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false);
+}
+
+template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
+  vcycle<T>(c, which, 0, b, x, true);
+  for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, b, x, false);
+}
+
+// ---------------------------------------------------------------------------
+// preconditioned CG. The residual norm of step k is copied to the host while
+// the preconditioner of step k+1 runs, so the GPU never idles on the check.
+// ---------------------------------------------------------------------------
+template <class T, class Op, class Pre>
+static int pcg(stokes_ctx& c, size_t n, Op&& op, Pre&& pre, const T* b, T* x, double rtol, int maxit,
+               bool* converged = nullptr) {
+  Scalars& S = c.sc;
+  const int s = S.take(5);
+  double* D = S.d + s;  // 0,1: r.z (alternating), 2: d.q, 3: r.r, 4: b.b
+  Tmp<T> r(c.pool, n), z(c.pool, n), d(c.pool, n), q(c.pool, n);
+  zero<T>(c, x, n);
+  copy<T>(c, r, b, n);
+  dot1<T>(c, (const T*)r, (const T*)r, n, D + 4);
+  double bb = read_now(c, D + 4, s + 4);
+  if (!std::isfinite(bb)) throw Error(STOKES_ERR_NAN, "non-finite right-hand side in an inner solve");
+  if (converged) *converged = true;
+  if (bb == 0.0) {
+    S.give(5);
+    return 0;
+  }
+  const double bn = std::sqrt(bb);
+  pre((const T*)r, (T*)z);
+  copy<T>(c, d, z, n);
+  int irz = 0, irzn = 1;
+  dot1<T>(c, (const T*)r, (const T*)z, n, D + irz);
+  int it = 0;
+  bool done = false;
+  while (it < maxit) {
+    op((const T*)d, (T*)q);
+    dot1<T>(c, (const T*)d, (const T*)q, n, D + 2);
+    cg_update<T>(c.ex, n, Coef::ratio(D + irz, D + 2), d, x, q, r);
+    ++it;
+    dot1<T>(c, (const T*)r, (const T*)r, n, D + 3);
+    read_issue(c, D + 3, s + 3);
+    pre((const T*)r, (T*)z);
+    double rr = read_wait(c, s + 3);
+    if (!std::isfinite(rr)) throw Error(STOKES_ERR_NAN, "non-finite residual in an inner solve");
+    if (std::sqrt(rr) <= rtol * bn) {
+      done = true;
+      break;
+    }
+    dot1<T>(c, (const T*)r, (const T*)z, n, D + irzn);
+    axpby<T>(c.ex, n, Coef::constant(1.0), z, Coef::ratio(D + irzn, D + irz), d);
+    std::swap(irz, irzn);
+  }
+  if (converged) *converged = done;
+  S.give(5);
+  return it;
+}
+
+// ---------------------------------------------------------------------------
+// velocity operator and its inverse
+// ---------------------------------------------------------------------------
+// y = A x  (+ gamma mu B^T M_Q^{-1} B x for the augmented Lagrangian, Eq. def_of_Alambda)
+template <class T> static void op_A(stokes_ctx& c, const T* x, T* y) {
+  bsr3_apply<T>(c.ex, c.A, x, y, (const T*)nullptr);
+  if (c.gamma > 0.0) {
+    size_t np = npres(c);
+    Tmp<T> bx(c.pool, np), mb(c.pool, np);
+    b_apply<T>(c.ex, c.B, x, bx, (const T*)nullptr, 1.0);
+    mass_inverse<T>(c, bx, mb, c.opt.mass_steps_al);
+    bt_apply<T>(c.ex, c.Bt, mb, y, (const T*)nullptr, y, c.gamma * c.mu);
+  }
+}
+
+// A^{-1} t by PCG preconditioned with `vcycles` V-cycles of A~_3 (Sec. 5.2:
+// CG with (A~_{lambda,3})_2Vc)
+template <class T> static int ainv(stokes_ctx& c, const T* t, T* w, double tol) {
+  bool ok = true;
+  int it = pcg<T>(
+      c, nvel(c), [&](const T* x, T* y) { op_A<T>(c, x, y); },
+      [&](const T* r, T* z) { vcycles<T>(c, 0, r, z, std::max(1, c.opt.vcycles)); }, t, w, tol, c.opt.max_inner, &ok);
+  c.inner_iters += it;
+  if (!ok) c.inner_capped = true;
+  return it;
+}
+
+// ---------------------------------------------------------------------------
+// Cahouet-Chabard preconditioner (Eqs. Schur_complement_preconditioners):
+//   C r = mu (1 + gamma) M_Q^{-1} r + dt^{-1} T^{-1} r,
+//   T = B Lambda_V^{-1} B^T (C^Lambda) or L_Q (C^Delta), solved by PCG with one
+//   V-cycle of eps M_Q + L_Q as preconditioner (Sec. 4.2), on the complement
+//   of the constants.
+// ---------------------------------------------------------------------------
+template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
+  size_t np = npres(c), nv = nvel(c);
+  Tmp<T> rp(c.pool, np), z1(c.pool, np), z2(c.pool, np);
+  copy<T>(c, rp, r, np);
+  project_mean<T>(c, rp, np);
+  mass_inverse<T>(c, rp, z1, c.opt.mass_steps);
+  const bool lumped = c.opt.schur_prec == STOKES_SCHUR_PREC_LUMPED;
+  const T* linv = pick<T>(c.lumped_inv64, c.lumped_inv32);
+  int it = pcg<T>(
+      c, np,
+      [&](const T* p, T* y) {
+        if (lumped) {
+          Tmp<T> t(c.pool, nv);
+          bt_apply<T>(c.ex, c.Bt, p, t, linv, (const T*)nullptr, 1.0);
+          b_apply<T>(c.ex, c.B, t, y, (const T*)nullptr, 1.0);
+        } else {
+          spmv_store<T>(c.ex, c.LQ, 1, p, y, STOKES_KERNEL_SPMV_P1);
+        }
+        project_mean<T>(c, y, np);
+      },
+      [&](const T* v, T* w) {
+        Tmp<T> vp(c.pool, np);
+        copy<T>(c, vp, v, np);
+        project_mean<T>(c, vp, np);
+        vcycles<T>(c, 1, vp, w, 1);
+      },
+      (const T*)rp, (T*)z2, c.opt.schur_inner_tol, c.opt.max_inner);
+  c.schur_inner_iters += it;
+  lincomb2<T>(c.ex, np, c.mu * (1.0 + c.gamma), z1, 1.0 / c.dt, z2, z);
+}
+
+// ---------------------------------------------------------------------------
+// Method 1 on a residual system K [dU; dP] = [rF; rg]:
+//   w = A_g^{-1} rF_g,  S dP = rg - B w  by flexible CG (Polak-Ribiere beta,
+//   Notay 2000) preconditioned with C,  dU = w + sum_k alpha_k A_g^{-1} B^T d_k.
+// With gamma > 0 the first block row is A_gamma dU - B^T dP = rF + gamma mu
+// B^T M_Q^{-1} rg, which has the same solution (Eqs. LA_problem,
+// Schur_LA_problem).
+// ---------------------------------------------------------------------------
+template <class T>
+static void method1(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, double eta, double tol_in) {
+  const size_t nv = nvel(c), np = npres(c);
+  Tmp<T> Fg(c.pool, nv);
+  const T* F = rF;
+  if (c.gamma > 0.0) {
+    Tmp<T> mg(c.pool, np);
+    mass_inverse<T>(c, rg, mg, c.opt.mass_steps_al);
+    bt_apply<T>(c.ex, c.Bt, mg, Fg, (const T*)nullptr, rF, c.gamma * c.mu);
+    F = Fg;
+  }
+  ainv<T>(c, F, dU, tol_in);
+  zero<T>(c, dP, np);
+  Tmp<T> r(c.pool, np), z(c.pool, np), d(c.pool, np), q(c.pool, np), rold(c.pool, np);
+  Tmp<T> t(c.pool, nv), wd(c.pool, nv);
+  b_apply<T>(c.ex, c.B, dU, r, rg, -1.0);  // r = rg - B w
+  project_mean<T>(c, r, np);
+  Scalars& S = c.sc;
+  const int s = S.take(6);
+  double* D = S.d + s;  // 0,2: z.r (alternating) 1: d.q 3: z.r_old 4: r.r 5: beta numerator
+  dot1<T>(c, (const T*)r, (const T*)r, np, D + 4);
+  double rr0 = read_now(c, D + 4, s + 4);
+  if (!std::isfinite(rr0)) throw Error(STOKES_ERR_NAN, "non-finite Schur right-hand side");
+  if (rr0 == 0.0) {
+    S.give(6);
+    return;
+  }
+  cprec<T>(c, r, z);
+  copy<T>(c, d, z, np);
+  int irz = 0, irzn = 2;
+  dot1<T>(c, (const T*)z, (const T*)r, np, D + irz);
+  int k = 0;
+  bool done = false;
+  while (k < c.opt.max_outer) {
+    bt_apply<T>(c.ex, c.Bt, d, t, (const T*)nullptr, (const T*)nullptr, 1.0);  // t = B^T d
+    ainv<T>(c, t, wd, tol_in);                                                  // wd = A^{-1} t
+    b_apply<T>(c.ex, c.B, wd, q, (const T*)nullptr, 1.0);                       // q = S d
+    dot1<T>(c, (const T*)d, (const T*)q, np, D + 1);
+    Coef alpha = Coef::ratio(D + irz, D + 1);
+    cg_update<T>(c.ex, np, alpha, d, dP, (const T*)nullptr, (T*)nullptr);
+    cg_update<T>(c.ex, nv, alpha, wd, dU, (const T*)nullptr, (T*)nullptr);
+    copy<T>(c, rold, r, np);
+    axpby<T>(c.ex, np, Coef::ratio(D + irz, D + 1, -1.0), q, Coef::constant(1.0), r);
+    project_mean<T>(c, r, np);
+    ++k;
+    dot1<T>(c, (const T*)r, (const T*)r, np, D + 4);
+    read_issue(c, D + 4, s + 4);
+    cprec<T>(c, r, z);
+    double rr = read_wait(c, s + 4);
+    if (!std::isfinite(rr)) throw Error(STOKES_ERR_NAN, "non-finite Schur residual");
+    if (std::sqrt(rr) <= eta * std::sqrt(rr0)) {
+      done = true;
+      break;
+    }
+    const T* xs[2] = {z, z};
+    const T* ys[2] = {r, rold};
+    double tmp2[1];
+    (void)tmp2;
+    dots<T>(c.ex, c.ds, 1, xs, ys, np, D + irzn);
+    dots<T>(c.ex, c.ds, 1, xs + 1, ys + 1, np, D + 3);
+    scalar_sub(c.ex, D + 5, D + irzn, D + 3);
+    axpby<T>(c.ex, np, Coef::constant(1.0), z, Coef::ratio(D + 5, D + irz), d);
+    std::swap(irz, irzn);
+  }
+  c.outer_iters += k;
+  if (!done) c.outer_capped = true;
+  S.give(6);
+}
+
+// ---------------------------------------------------------------------------
+// Method 2: right-preconditioned FGMRES(m) on the coupled system
+//   [A_g  -B^T; B  0] (Sec. 2.4), preconditioner (Eq.
+//   inexact_factorization_of_Alambda)
+//   P^{-1} = [I  A~^{-1}B^T; 0 I] diag(A~^{-1}, C) [I 0; -B A~^{-1} I]
+// or its block-triangular form without the left factor (Remark "Alternative
+// preconditioner"). A~^{-1} = V-cycles of A~_3 or PCG on A_g to inner_tol.
+// Arnoldi with classical Gram-Schmidt applied twice (CGS2), FP64 Hessenberg
+// and Givens rotations on the host.
+// ---------------------------------------------------------------------------
+template <class T> static void atilde_inv(stokes_ctx& c, const T* r, T* z, double tol_in) {
+  if (c.opt.m2_inner_cg)
+    ainv<T>(c, r, z, tol_in);
+  else
+    vcycles<T>(c, 0, r, z, std::max(1, c.opt.vcycles));
+}
+
+template <class T> static void block_prec(stokes_ctx& c, const T* ru, const T* rp, T* zu, T* zp, double tol_in) {
+  const size_t nv = nvel(c), np = npres(c);
+  Tmp<T> w(c.pool, nv), s(c.pool, np);
+  atilde_inv<T>(c, ru, w, tol_in);                       // w = A~^{-1} ru
+  b_apply<T>(c.ex, c.B, w, s, rp, -1.0);                 // s = rp - B w
+  cprec<T>(c, s, zp);                                    // zp = C s
+  if (c.opt.block_lu) {
+    Tmp<T> t(c.pool, nv), v(c.pool, nv);
+    bt_apply<T>(c.ex, c.Bt, zp, t, (const T*)nullptr, (const T*)nullptr, 1.0);
+    atilde_inv<T>(c, t, v, tol_in);                      // v = A~^{-1} B^T zp
+    lincomb2<T>(c.ex, nv, 1.0, w, 1.0, v, zu);           // zu = w + v
+  } else {
+    copy<T>(c, zu, (const T*)w, nv);
+  }
+}
+
+template <class T>
+static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, double eta, double tol_in) {
+  const size_t nv = nvel(c), np = npres(c), N = nv + np;
+  const int m = std::max(2, c.opt.restart);
+  // Krylov basis V (m+1 vectors) and flexible basis Z (m vectors), each [u; p]
+  std::vector<Tmp<T>*> V, Z;
+  for (int j = 0; j <= m; ++j) V.push_back(new Tmp<T>(c.pool, N));
+  for (int j = 0; j < m; ++j) Z.push_back(new Tmp<T>(c.pool, N));
+  auto cleanup = [&]() {
+    for (auto* p : V) delete p;
+    for (auto* p : Z) delete p;
+  };
+  Scalars& S = c.sc;
+  const int s = S.take(2 * (m + 1) + 2);
+  double* D = S.d + s;
+  try {
+    Tmp<T> Fg(c.pool, nv);
+    const T* F = rF;
+    if (c.gamma > 0.0) {
+      Tmp<T> mg(c.pool, np);
+      mass_inverse<T>(c, rg, mg, c.opt.mass_steps_al);
+      bt_apply<T>(c.ex, c.Bt, mg, Fg, (const T*)nullptr, rF, c.gamma * c.mu);
+      F = Fg;
+    }
+    zero<T>(c, dU, nv);
+    zero<T>(c, dP, np);
+    // r0 = [F; rg]
+    T* v0 = *V[0];
+    copy<T>(c, v0, F, nv);
+    copy<T>(c, v0 + nv, rg, np);
+    project_mean<T>(c, v0 + nv, np);
+    dot1<T>(c, (const T*)v0, (const T*)v0, N, D);
+    double beta0 = std::sqrt(read_now(c, D, s));
+    if (!std::isfinite(beta0)) throw Error(STOKES_ERR_NAN, "non-finite coupled right-hand side");
+    double beta = beta0;
+    int total = 0;
+    bool done = beta0 == 0.0;
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1);
+    while (!done && total < c.opt.max_outer) {
+      scale_copy<T>(c.ex, N, Coef::constant(1.0 / beta), *V[0], *V[0]);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int j = 0;
+      for (; j < m && total < c.opt.max_outer; ++j, ++total) {
+        T* vj = *V[j];
+        T* zj = *Z[j];
+        T* w = *V[j + 1];
+        block_prec<T>(c, vj, vj + nv, zj, zj + nv, tol_in);
+        // w = K zj
+        op_A<T>(c, zj, w);
+        bt_apply<T>(c.ex, c.Bt, zj + nv, w, (const T*)nullptr, w, -1.0);
+        b_apply<T>(c.ex, c.B, zj, w + nv, (const T*)nullptr, 1.0);
+        // CGS2: two passes of h = V^T w, w -= V h
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int i = 0; i <= j; i += kMaxDots) {
+            int k = std::min(kMaxDots, j + 1 - i);
+            const T* xs[kMaxDots];
+            const T* ys[kMaxDots];
+            for (int t = 0; t < k; ++t) xs[t] = *V[i + t], ys[t] = w;
+            dots<T>(c.ex, c.ds, k, xs, ys, N, D + 2 + (pass ? m + 1 : 0) + i);
+          }
+          for (int i = 0; i <= j; ++i)
+            axpby<T>(c.ex, N, Coef::ratio(D + 2 + (pass ? m + 1 : 0) + i, nullptr, -1.0), *V[i],
+                     Coef::constant(1.0), w);
+        }
+        dot1<T>(c, (const T*)w, (const T*)w, N, D + 1);
+        SK_CUDA(cudaMemcpyAsync(S.h + s + 1, D + 1, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost,
+                                c.ex.s));
+        SK_CUDA(cudaStreamSynchronize(c.ex.s));
+        double hn = std::sqrt(S.h[s + 1]);
+        for (int i = 0; i <= j; ++i) H[i * m + j] = S.h[s + 2 + i] + S.h[s + 2 + m + 1 + i];
+        H[(j + 1) * m + j] = hn;
+        if (!std::isfinite(hn)) throw Error(STOKES_ERR_NAN, "non-finite Arnoldi vector");
+        if (hn > 0) scale_copy<T>(c.ex, N, Coef::constant(1.0 / hn), w, w);
+        // Givens
+        for (int i = 0; i < j; ++i) {
+          double a = H[i * m + j], b = H[(i + 1) * m + j];
+          H[i * m + j] = cs[i] * a + sn[i] * b;
+          H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+        }
+        double a = H[j * m + j], b = H[(j + 1) * m + j];
+        double rden = std::hypot(a, b);
+        cs[j] = rden > 0 ? a / rden : 1.0;
+        sn[j] = rden > 0 ? b / rden : 0.0;
+        H[j * m + j] = rden;
+        H[(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        if (std::fabs(g[j + 1]) <= eta * beta0 || hn == 0.0) {
+          ++j;
+          ++total;
+          done = true;
+          break;
+        }
+      }
+      // y = H^{-1} g (upper triangular j x j), x += Z y
+      std::vector<double> y(j);
+      for (int i = j - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k < j; ++k) t -= H[i * m + k] * y[k];
+        y[i] = t / H[i * m + i];
+      }
+      for (int i = 0; i < j; ++i) {
+        cg_update<T>(c.ex, nv, Coef::constant(y[i]), (const T*)*Z[i], dU, (const T*)nullptr, (T*)nullptr);
+        cg_update<T>(c.ex, np, Coef::constant(y[i]), (const T*)(*Z[i] + nv), dP, (const T*)nullptr, (T*)nullptr);
+      }
+      if (done || total >= c.opt.max_outer) break;
+      // restart: r = [F; rg] - K x
+      T* r0 = *V[0];
+      op_A<T>(c, dU, r0);
+      bt_apply<T>(c.ex, c.Bt, dP, r0, (const T*)nullptr, r0, -1.0);
+      axpby<T>(c.ex, nv, Coef::constant(1.0), F, Coef::constant(-1.0), r0);
+      b_apply<T>(c.ex, c.B, dU, r0 + nv, rg, -1.0);
+      project_mean<T>(c, r0 + nv, np);
+      dot1<T>(c, (const T*)r0, (const T*)r0, N, D);
+      beta = std::sqrt(read_now(c, D, s));
+      if (beta <= eta * beta0) done = true;
+    }
+    c.outer_iters += total;
+    if (!done) c.outer_capped = true;
+  } catch (...) {
+    S.give(2 * (m + 1) + 2);
+    cleanup();
+    throw;
+  }
+  S.give(2 * (m + 1) + 2);
+  cleanup();
+}
+
+// ---------------------------------------------------------------------------
+// defect correction on the FP64 residual of the full system
+// ---------------------------------------------------------------------------
+template <class T>
+static void correction(stokes_ctx& c, const double* rF, const double* rg, double* U, double* P, double eta,
+                       double tol_in) {
+  const size_t nv = nvel(c), np = npres(c);
+  Tmp<T> dU(c.pool, nv), dP(c.pool, np);
+  const T* rFt;
+  const T* rgt;
+  Tmp<T> rF32(c.pool, std::is_same<T, double>::value ? 1 : nv), rg32(c.pool, std::is_same<T, double>::value ? 1 : np);
+  if constexpr (std::is_same<T, double>::value) {
+    rFt = rF;
+    rgt = rg;
+  } else {
+    convert<double, float>(c.ex, nv, rF, rF32);
+    convert<double, float>(c.ex, np, rg, rg32);
+    rFt = rF32;
+    rgt = rg32;
+  }
+  if (c.opt.method == STOKES_METHOD_COUPLED)
+    method2<T>(c, rFt, rgt, dU, dP, eta, tol_in);
+  else
+    method1<T>(c, rFt, rgt, dU, dP, eta, tol_in);
+  add_convert<T, double>(c.ex, nv, dU, U);
+  add_convert<T, double>(c.ex, np, dP, P);
+}
+
+// full residual rF = F - A U + B^T P, rg = g - B U and its relative norm
+static double full_residual(stokes_ctx& c, const double* F, const double* g, const double* U, const double* P,
+                            double* rF, double* rg, double normFg) {
+  const size_t nv = nvel(c), np = npres(c);
+  bsr3_apply<double>(c.ex, c.A, U, rF, F);
+  bt_apply<double>(c.ex, c.Bt, P, rF, (const double*)nullptr, rF, 1.0);
+  b_apply<double>(c.ex, c.B, U, rg, g, -1.0);
+  const int s = c.sc.take(2);
+  const double* xs[2] = {rF, rg};
+  dots<double>(c.ex, c.ds, 1, xs, xs, nv, c.sc.d + s);
+  dots<double>(c.ex, c.ds, 1, xs + 1, xs + 1, np, c.sc.d + s + 1);
+  SK_CUDA(cudaMemcpyAsync(c.sc.h + s, c.sc.d + s, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  double rr = c.sc.h[s] + c.sc.h[s + 1];
+  c.sc.give(2);
+  return std::sqrt(rr) / normFg;
+}
+
+// Solve K [U; P] = [F; g] in the reduced spaces (interior velocity, all P1
+// nodes) to a true relative residual tol; P is normalised to int p_h = 0.
+static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double tol, double* U, double* P,
+                         stokes_info* info, std::chrono::steady_clock::time_point t0) {
+  const size_t nv = nvel(c), np = npres(c);
+  c.outer_iters = c.inner_iters = c.schur_inner_iters = 0;
+  c.outer_capped = c.inner_capped = false;
+  SK_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.ex.s));
+  set_breakdown_flag(c.d_flag);
+  Tmp<double> gz(c.pool, np), rF(c.pool, nv), rg(c.pool, np);
+  const double* gp = g;
+  if (!gp) {
+    zero<double>(c, gz, np);
+    gp = gz;
+  }
+  // compatibility of g: sum(g) = 0 (1^T B = 0)
+  const int s = c.sc.take(3);
+  {
+    const double* xs[1] = {gp};
+    dots<double>(c.ex, c.ds, 1, xs, (const double* const*)nullptr, np, c.sc.d + s);
+    dots<double>(c.ex, c.ds, 1, xs, xs, np, c.sc.d + s + 1);
+    const double* fs[1] = {F};
+    dots<double>(c.ex, c.ds, 1, fs, fs, nv, c.sc.d + s + 2);
+    SK_CUDA(cudaMemcpyAsync(c.sc.h + s, c.sc.d + s, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
+    SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  }
+  double gsum = c.sc.h[s], gg = c.sc.h[s + 1], FF = c.sc.h[s + 2];
+  c.sc.give(3);
+  if (!std::isfinite(gsum) || !std::isfinite(gg) || !std::isfinite(FF))
+    throw Error(STOKES_ERR_NAN, "non-finite right-hand side");
+  if (std::fabs(gsum) > 1e-10 * std::sqrt((double)np * gg) + 1e-300)
+    throw Error(STOKES_ERR_INCOMPATIBLE_RHS, "sum(g) must vanish for B u = g to be solvable");
+  double normFg = std::sqrt(FF + gg);
+  zero<double>(c, U, nv);
+  zero<double>(c, P, np);
+  int status = STOKES_OK;
+  double rel = 0.0;
+  int pass = 0;
+  if (normFg > 0) {
+    for (;; ++pass) {
+      rel = full_residual(c, F, gp, U, P, rF, rg, normFg);
+      if (!std::isfinite(rel)) {
+        status = STOKES_ERR_NAN;
+        break;
+      }
+      if (rel <= tol) break;
+      if (pass >= c.opt.max_refine) {
+        status = STOKES_ERR_NOT_CONVERGED;
+        break;
+      }
+      if (c.mixed) {
+        // FP32 inner work: one pass gains ~4 digits
+        double eta = std::max(1e-4, 0.5 * tol / rel), tin = std::max(c.opt.inner_tol, 1e-5);
+        correction<float>(c, rF, rg, U, P, eta, tin);
+      } else {
+        double eta = std::max(0.5 * tol / rel, 1e-13);
+        correction<double>(c, rF, rg, U, P, eta, c.opt.inner_tol);
+      }
+    }
+  }
+  // int p_h = 0: P -= (M_Q 1 . P) / (1^T M_Q 1)
+  {
+    const int s2 = c.sc.take(1);
+    dot1<double>(c, (const double*)c.MQ1, (const double*)P, np, c.sc.d + s2);
+    sub_mean<double>(c.ex, np, c.sc.d + s2, c.MQ1_sum, P);
+    c.sc.give(1);
+  }
+  int flag = 0;
+  SK_CUDA(cudaMemcpyAsync(&flag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  if (status == STOKES_OK && (flag & 1) && rel > tol) status = STOKES_ERR_BREAKDOWN;
+  if (info) {
+    info->outer_iters = c.outer_iters;
+    info->inner_iters = c.inner_iters;
+    info->refinements = pass;
+    info->status = status;
+    info->rel_residual = rel;
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+int solve_context(stokes_ctx* cp, const double* f, const double* g, double tol, double* u, double* p,
+                  stokes_info* info) {
+  stokes_ctx& c = *cp;
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t nv = nvel(c), np = npres(c);
+  Tmp<double> F(c.pool, nv);
+  assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, f, F);
+  int status = solve_reduced(c, F, g, tol, c.U_last, c.P_last, info, t0);
+  expand_velocity(c.ex, c.n, c.U_last, u);
+  copy<double>(c, p, (const double*)c.P_last, np);
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  c.have_solution = true;
+  if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+// Adjoint. K = [A -B^T; B 0] has K^T = [A B^T; -B 0]; with lp = -P' the
+// transposed system K^T [lu; lp] = [jU; jP] is the forward system
+// K [lu; P'] = [jU; -jP]. J depends on the normalised pressure, so jP is first
+// projected with (I - m 1^T / 1^T m)^T, m = M_Q 1, which makes sum(jP) = 0.
+// Then dJ/dF = lu, dJ/dg = lp, dJ/df = M_V^T lu (all nodes), and
+// dJ/dmu = -lu^T (dA/dmu) U = -lu^T E_V U, with E_V U = (A U - M_V U / dt) / mu
+// (the augmented-Lagrangian form has the same solution for every gamma).
+int adjoint_context(stokes_ctx* cp, const double* dJdu, const double* dJdp, double tol, double* dJdf,
+                    double* dJdg, double* dJdmu, stokes_info* info) {
+  stokes_ctx& c = *cp;
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t nv = nvel(c), np = npres(c);
+  Tmp<double> jU(c.pool, nv), jP(c.pool, np), lu(c.pool, nv), lp(c.pool, np);
+  restrict_velocity(c.ex, c.n, dJdu, jU);
+  if (dJdp) {
+    // jP <- -(jP - m (1.jP) / (1.m))  (projected and negated)
+    const int s = c.sc.take(1);
+    copy<double>(c, jP, dJdp, np);
+    dot1<double>(c, (const double*)jP, (const double*)nullptr, np, c.sc.d + s);
+    Tmp<double> t(c.pool, np);
+    scale_copy<double>(c.ex, np, Coef::ratio(c.sc.d + s, nullptr, 1.0 / c.MQ1_sum), c.MQ1, t);
+    lincomb2<double>(c.ex, np, -1.0, jP, 1.0, t, jP);
+    c.sc.give(1);
+  } else {
+    zero<double>(c, jP, np);
+  }
+  int status = solve_reduced(c, jU, jP, tol, lu, lp, info, t0);
+  // dJ/df = M_V^T lu on all nodes
+  assemble_load_transpose(c.ex, c.n, c.lv[0].X, lu, dJdf);
+  if (dJdg) scale_copy<double>(c.ex, np, Coef::constant(-1.0), lp, dJdg);
+  if (dJdmu) {
+    Tmp<double> AU(c.pool, nv), MU(c.pool, nv);
+    size_t N = (size_t)(2 * c.n + 1) * (2 * c.n + 1) * (2 * c.n + 1);
+    Tmp<double> Uall(c.pool, 3 * N);
+    bsr3_apply<double>(c.ex, c.A, c.U_last, AU, (const double*)nullptr);
+    expand_velocity(c.ex, c.n, c.U_last, Uall);
+    assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, Uall, MU);
+    lincomb2<double>(c.ex, nv, 1.0 / c.mu, AU, -1.0 / (c.mu * c.dt), MU, AU);  // E_V U
+    const int s = c.sc.take(1);
+    dot1<double>(c, (const double*)lu, (const double*)AU, nv, c.sc.d + s);
+    *dJdmu = -read_now(c, c.sc.d + s, s);
+    c.sc.give(1);
+  }
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// operator access for tests (FP64)
+// ---------------------------------------------------------------------------
+void apply_operator(stokes_ctx* cp, int op, int level, const double* x, double* y) {
+  stokes_ctx& c = *cp;
+  SK_REQUIRE(level >= 0 && level < (int)c.lv.size(), STOKES_ERR_ARG, "level out of range");
+  const Level& L = c.lv[level];
+  if (op != STOKES_OP_A3 && op != STOKES_OP_KQ && op != STOKES_OP_VCYCLE_A3 && op != STOKES_OP_PROLONG_P2 &&
+      op != STOKES_OP_RESTRICT_P2 && op != STOKES_OP_PROLONG_P1)
+    SK_REQUIRE(level == 0, STOKES_ERR_ARG, "operator defined on level 0 only");
+  const size_t np = npres(c), nv = nvel(c);
+  switch (op) {
+    case STOKES_OP_A: bsr3_apply<double>(c.ex, c.A, x, y, nullptr); break;
+    case STOKES_OP_A3: spmv_store<double>(c.ex, L.A3, 3, x, y, STOKES_KERNEL_SPMM_A3); break;
+    case STOKES_OP_B: b_apply<double>(c.ex, c.B, x, y, nullptr, 1.0); break;
+    case STOKES_OP_BT: bt_apply<double>(c.ex, c.Bt, x, y, nullptr, nullptr, 1.0); break;
+    case STOKES_OP_MQ: spmv_store<double>(c.ex, c.MQ, 1, x, y, STOKES_KERNEL_SPMV_P1); break;
+    case STOKES_OP_LQ: spmv_store<double>(c.ex, c.LQ, 1, x, y, STOKES_KERNEL_SPMV_P1); break;
+    case STOKES_OP_KQ: spmv_store<double>(c.ex, L.KQ, 1, x, y, STOKES_KERNEL_SPMV_P1); break;
+    case STOKES_OP_LUMPED_INV: {
+      // y = Lambda^{-1} x per node and component
+      Tmp<double> ones(c.pool, 1);
+      (void)ones;
+      SK_CUDA(cudaMemcpyAsync(y, x, nv * sizeof(double), cudaMemcpyDeviceToDevice, c.ex.s));
+      cheb_first<double>(c.ex, nv, 3, c.lumped_inv64, x, 1.0, y, y);
+      break;
+    }
+    case STOKES_OP_VCYCLE_A3: {
+      SK_REQUIRE(level == 0, STOKES_ERR_ARG, "V-cycle from level 0 only");
+      vcycles<double>(c, 0, x, y, std::max(1, c.opt.vcycles));
+      break;
+    }
+    case STOKES_OP_VCYCLE_KQ: vcycles<double>(c, 1, x, y, 1); break;
+    case STOKES_OP_SCHUR_PREC: cprec<double>(c, x, y); break;
+    case STOKES_OP_SCHUR: {
+      Tmp<double> t(c.pool, nv), w(c.pool, nv);
+      bt_apply<double>(c.ex, c.Bt, x, t, nullptr, nullptr, 1.0);
+      ainv<double>(c, t, w, c.opt.inner_tol);
+      b_apply<double>(c.ex, c.B, w, y, nullptr, 1.0);
+      break;
+    }
+    case STOKES_OP_AGAMMA: op_A<double>(c, x, y); break;
+    case STOKES_OP_PROLONG_P2:
+      SK_REQUIRE(level + 1 < (int)c.lv.size(), STOKES_ERR_ARG, "no coarser level");
+      spmv_store<double>(c.ex, L.P2, 3, x, y, STOKES_KERNEL_TRANSFER);
+      break;
+    case STOKES_OP_RESTRICT_P2:
+      SK_REQUIRE(level + 1 < (int)c.lv.size(), STOKES_ERR_ARG, "no coarser level");
+      spmv_store<double>(c.ex, L.R2, 3, x, y, STOKES_KERNEL_TRANSFER);
+      break;
+    case STOKES_OP_PROLONG_P1:
+      SK_REQUIRE(level + 1 < (int)c.lv.size(), STOKES_ERR_ARG, "no coarser level");
+      spmv_store<double>(c.ex, L.P1, 1, x, y, STOKES_KERNEL_TRANSFER);
+      break;
+    case STOKES_OP_LOAD: assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, x, y); break;
+    default: throw Error(STOKES_ERR_ARG, "unknown operator");
+  }
+  (void)np;
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+}
+
+// ---------------------------------------------------------------------------
+// setup helpers that need the solver kernels
+// ---------------------------------------------------------------------------
+// lambda_max(D^{-1} M) from the Lanczos tridiagonal of `steps` Jacobi-PCG
+// steps (the CG coefficients give the Lanczos matrix; Golub & Van Loan 10.2).
+double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps, uint64_t seed) {
+  const size_t n = M.rows;
+  if (n == 0) return 1.0;
+  std::vector<double> hb(n);
+  uint64_t st = seed * 0x9E3779B97F4A7C15ULL + 1;
+  for (size_t i = 0; i < n; ++i) {
+    st += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    hb[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+  Tmp<double> r(c.pool, n), z(c.pool, n), d(c.pool, n), q(c.pool, n), tmp(c.pool, n);
+  SK_CUDA(cudaMemcpyAsync(r, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c.ex.s));
+  const int s = c.sc.take(3);
+  double* D = c.sc.d + s;
+  cheb_first<double>(c.ex, n, 1, dinv, r, 1.0, z, tmp);
+  copy<double>(c, d, z, n);
+  dot1<double>(c, (const double*)r, (const double*)z, n, D);
+  double rz = read_now(c, D, s);
+  std::vector<double> al, be;
+  for (int j = 0; j < steps; ++j) {
+    spmv_store<double>(c.ex, M, 1, d, q, -1);
+    dot1<double>(c, (const double*)d, (const double*)q, n, D + 1);
+    double dq = read_now(c, D + 1, s + 1);
+    if (!(dq > 0) || !(rz > 0)) break;
+    double a = rz / dq;
+    cg_update<double>(c.ex, n, Coef::constant(a), d, tmp, q, r);
+    cheb_first<double>(c.ex, n, 1, dinv, r, 1.0, z, tmp);
+    dot1<double>(c, (const double*)r, (const double*)z, n, D + 2);
+    double rzn = read_now(c, D + 2, s + 2);
+    double b = rzn / rz;
+    al.push_back(a);
+    be.push_back(b);
+    axpby<double>(c.ex, n, Coef::constant(1.0), z, Coef::constant(b), d);
+    rz = rzn;
+    if (!(rz > 0)) break;
+  }
+  c.sc.give(3);
+  int k = (int)al.size();
+  SK_REQUIRE(k > 0, STOKES_ERR_ARG, "spectrum estimate failed (matrix not positive definite?)");
+  std::vector<double> dg(k), off(k > 1 ? k - 1 : 1);
+  for (int j = 0; j < k; ++j) {
+    dg[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < k) off[j] = std::sqrt(be[j]) / al[j];
+  }
+  // largest eigenvalue of the symmetric tridiagonal by Sturm bisection
+  double hi = 0;
+  for (int j = 0; j < k; ++j)
+    hi = std::max(hi, dg[j] + (j > 0 ? std::fabs(off[j - 1]) : 0) + (j + 1 < k ? std::fabs(off[j]) : 0));
+  double lo = 0;
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int j = 0; j < k; ++j) {
+      q = dg[j] - x - (j > 0 ? off[j - 1] * off[j - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 100; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= k) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+}  // namespace sk

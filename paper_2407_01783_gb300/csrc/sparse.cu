@@ -1,0 +1,400 @@
+// Sparse products for the Stokes operators: vectorised CSR (G threads per row,
+// shuffle reduction inside the group) over scalar, 3x3, 1x3 and 3x1 blocks,
+// with fused epilogues (store, residual, accumulate, Chebyshev update, row
+// scaling). All of it is HBM-bound: the matrix is streamed once per product
+// (coalesced, values stored as planes of nnz entries), the gathered vector
+// mostly hits L2. The number of threads per row is picked per matrix by a
+// timing sweep at setup.
+#include <cfloat>
+#include <cmath>
+
+#include "internal.h"
+
+namespace sk {
+
+// ---------------------------------------------------------------------------
+// profiling helpers
+// ---------------------------------------------------------------------------
+cudaEvent_t Prof::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  SK_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void Prof::reset() {
+  for (auto& r : rec) {
+    for (auto& p : r.ev) {
+      pool.push_back(p.first);
+      pool.push_back(p.second);
+    }
+    r.ev.clear();
+    r.bytes = 0;
+    r.launches = 0;
+  }
+}
+
+Prof::~Prof() {
+  reset();
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+ProfScope::ProfScope(const Exec& e, int k, double bytes) : ex(e), kind(k) {
+  if (ex.prof && ex.prof->on && kind >= 0) {
+    e1 = ex.prof->get();
+    cudaEventRecord(e1, ex.s);
+    ex.prof->rec[kind].bytes += bytes;
+    ex.prof->rec[kind].launches += 1;
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (e1) {
+    cudaEvent_t e2 = ex.prof->get();
+    cudaEventRecord(e2, ex.s);
+    ex.prof->rec[kind].ev.emplace_back(e1, e2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// epilogues: called by lane 0 of each row group with the row sums
+// ---------------------------------------------------------------------------
+template <class T, int NR> struct EpiStore {
+  T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) y[(size_t)row * NR + r] = acc[r];
+  }
+};
+template <class T, int NR> struct EpiAdd {
+  T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) y[(size_t)row * NR + r] += acc[r];
+  }
+};
+template <class T, int NR> struct EpiResid {  // y = b - acc
+  const T* b;
+  T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) y[(size_t)row * NR + r] = b[(size_t)row * NR + r] - acc[r];
+  }
+};
+template <class T, int NR> struct EpiAxpy {  // y = (b ? b : 0) + alpha * s_row * acc
+  const T* b;
+  const T* s;
+  T* y;
+  T alpha;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    T sc = s ? s[row] : T(1);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      T v = alpha * sc * acc[r];
+      if (b) v += b[(size_t)row * NR + r];
+      y[(size_t)row * NR + r] = v;
+    }
+  }
+};
+// Chebyshev semi-iteration step (Saad, Iterative Methods, Alg. 12.1):
+// r = b - A x_in; d = c1 d + c2 D^{-1} r; x_out = x_in + d.
+template <class T, int NR> struct EpiCheb {
+  const T* b;
+  const T* xin;
+  T* d;
+  T* xout;
+  const T* dinv;
+  T c1, c2;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    T di = dinv[row];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      size_t i = (size_t)row * NR + r;
+      T res = b[i] - acc[r];
+      T dn = c1 * d[i] + c2 * di * res;
+      d[i] = dn;
+      xout[i] = xin[i] + dn;
+    }
+  }
+};
+
+template <int G, class T, int NR>
+__device__ __forceinline__ void group_reduce(T* acc) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
+// scalar CSR, NR interleaved right-hand sides
+template <int G, int NR, class TM, class T, class Epi>
+__global__ void __launch_bounds__(256) k_csr(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                                             const TM* __restrict__ val, const T* __restrict__ x, Epi epi) {
+  int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = gt / G, lane = gt & (G - 1);
+  T acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = T(0);
+  if (row < rows) {
+    int e = rp[row + 1];
+    for (int k = rp[row] + lane; k < e; k += G) {
+      T a = (T)val[k];
+      size_t c = (size_t)col[k] * NR;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] += a * x[c + r];
+    }
+  }
+  group_reduce<G, T, NR>(acc);
+  if (row < rows && lane == 0) epi(row, acc);
+}
+
+// 3x3 blocks (strain-form A), planes v[(3c+d)*nnz + k]
+template <int G, class T, class Epi>
+__global__ void __launch_bounds__(256) k_bsr3(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                                              const T* __restrict__ v, long long nnz, const T* __restrict__ x, Epi epi) {
+  int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = gt / G, lane = gt & (G - 1);
+  T acc[3] = {T(0), T(0), T(0)};
+  if (row < rows) {
+    int e = rp[row + 1];
+    for (int k = rp[row] + lane; k < e; k += G) {
+      size_t c = (size_t)col[k] * 3;
+      T x0 = x[c], x1 = x[c + 1], x2 = x[c + 2];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        acc[r] += v[(size_t)(3 * r) * nnz + k] * x0 + v[(size_t)(3 * r + 1) * nnz + k] * x1 +
+                  v[(size_t)(3 * r + 2) * nnz + k] * x2;
+    }
+  }
+  group_reduce<G, T, 3>(acc);
+  if (row < rows && lane == 0) epi(row, acc);
+}
+
+// 1x3 blocks: B (P1 rows, interior P2 node columns)
+template <int G, class T, class Epi>
+__global__ void __launch_bounds__(256) k_b(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                                           const T* __restrict__ v, long long nnz, const T* __restrict__ x, Epi epi) {
+  int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = gt / G, lane = gt & (G - 1);
+  T acc[1] = {T(0)};
+  if (row < rows) {
+    int e = rp[row + 1];
+    for (int k = rp[row] + lane; k < e; k += G) {
+      size_t c = (size_t)col[k] * 3;
+      acc[0] += v[k] * x[c] + v[nnz + k] * x[c + 1] + v[2 * nnz + k] * x[c + 2];
+    }
+  }
+  group_reduce<G, T, 1>(acc);
+  if (row < rows && lane == 0) epi(row, acc);
+}
+
+// 3x1 blocks: B^T (interior P2 node rows, P1 columns)
+template <int G, class T, class Epi>
+__global__ void __launch_bounds__(256) k_bt(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                                            const T* __restrict__ v, long long nnz, const T* __restrict__ x, Epi epi) {
+  int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = gt / G, lane = gt & (G - 1);
+  T acc[3] = {T(0), T(0), T(0)};
+  if (row < rows) {
+    int e = rp[row + 1];
+    for (int k = rp[row] + lane; k < e; k += G) {
+      T xv = x[col[k]];
+      acc[0] += v[k] * xv;
+      acc[1] += v[nnz + k] * xv;
+      acc[2] += v[2 * nnz + k] * xv;
+    }
+  }
+  group_reduce<G, T, 3>(acc);
+  if (row < rows && lane == 0) epi(row, acc);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+enum Shape { SH_CSR1 = 0, SH_CSR3 = 1, SH_BSR3 = 2, SH_B = 3, SH_BT = 4 };
+
+template <int G, class T, class Epi>
+static void launch_g(const Exec& ex, const Csr& m, Shape sh, const T* x, const Epi& epi) {
+  const int bs = 256;
+  int grid = cdiv((long long)m.rows * G, bs);
+  if (grid == 0) return;
+  switch (sh) {
+    case SH_CSR1:
+      if constexpr (std::is_same<T, float>::value)
+        k_csr<G, 1, float, float, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v32, x, epi);
+      else
+        k_csr<G, 1, double, double, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, x, epi);
+      break;
+    case SH_CSR3:
+      if constexpr (std::is_same<T, float>::value)
+        k_csr<G, 3, float, float, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v32, x, epi);
+      else
+        k_csr<G, 3, double, double, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, x, epi);
+      break;
+    case SH_BSR3:
+      k_bsr3<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, epi);
+      break;
+    case SH_B:
+      k_b<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, epi);
+      break;
+    case SH_BT:
+      k_bt<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, epi);
+      break;
+  }
+  SK_CHECK_LAUNCH();
+}
+
+template <class T, class Epi>
+static void launch(const Exec& ex, const Csr& m, Shape sh, const T* x, const Epi& epi, int g) {
+  SK_REQUIRE(m.template v<T>() != nullptr, STOKES_ERR_ARG, "matrix values missing for this precision");
+  switch (g) {
+    case 1: launch_g<1>(ex, m, sh, x, epi); break;
+    case 2: launch_g<2>(ex, m, sh, x, epi); break;
+    case 4: launch_g<4>(ex, m, sh, x, epi); break;
+    case 8: launch_g<8>(ex, m, sh, x, epi); break;
+    case 16: launch_g<16>(ex, m, sh, x, epi); break;
+    default: launch_g<32>(ex, m, sh, x, epi); break;
+  }
+}
+
+// bytes: matrix once + x once (cols*NR) + y once (rows*NR) (+ extra epilogue streams)
+static double prod_bytes(const Csr& m, int esz, int nr_in, int nr_out, int extra_streams) {
+  return m.bytes(esz) + (double)esz * ((double)m.cols * nr_in + (double)m.rows * nr_out * (1 + extra_streams));
+}
+
+template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
+  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 0));
+  if (nr == 3) launch(ex, m, SH_CSR3, x, EpiStore<T, 3>{y}, m.group);
+  else launch(ex, m, SH_CSR1, x, EpiStore<T, 1>{y}, m.group);
+}
+template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
+  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 1));
+  if (nr == 3) launch(ex, m, SH_CSR3, x, EpiAdd<T, 3>{y}, m.group);
+  else launch(ex, m, SH_CSR1, x, EpiAdd<T, 1>{y}, m.group);
+}
+template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind) {
+  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 1));
+  if (nr == 3) launch(ex, m, SH_CSR3, x, EpiResid<T, 3>{b, y}, m.group);
+  else launch(ex, m, SH_CSR1, x, EpiResid<T, 1>{b, y}, m.group);
+}
+template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin, T* d, T* xout,
+                                  const T* dinv, double c1, double c2) {
+  int kind = nr == 3 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMV_P1;
+  // streams: b, x_in (own row), d read, d write, x_out write, dinv
+  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 4) + (double)sizeof(T) * m.rows);
+  if (nr == 3) launch(ex, m, SH_CSR3, xin, EpiCheb<T, 3>{b, xin, d, xout, dinv, (T)c1, (T)c2}, m.group);
+  else launch(ex, m, SH_CSR1, xin, EpiCheb<T, 1>{b, xin, d, xout, dinv, (T)c1, (T)c2}, m.group);
+}
+template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b) {
+  ProfScope ps(ex, STOKES_KERNEL_SPMV_A, prod_bytes(m, sizeof(T), 3, 3, b ? 1 : 0));
+  if (b) launch(ex, m, SH_BSR3, x, EpiResid<T, 3>{b, y}, m.group);
+  else launch(ex, m, SH_BSR3, x, EpiStore<T, 3>{y}, m.group);
+}
+template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha) {
+  ProfScope ps(ex, STOKES_KERNEL_B, m.bytes(sizeof(T)) + sizeof(T) * (3.0 * m.cols + m.rows * (b ? 2.0 : 1.0)));
+  launch(ex, m, SH_B, x, EpiAxpy<T, 1>{b, nullptr, y, (T)alpha}, m.group);
+}
+template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* scale, const T* b,
+                                 double alpha) {
+  ProfScope ps(ex, STOKES_KERNEL_BT, m.bytes(sizeof(T)) + sizeof(T) * (1.0 * m.cols + 3.0 * m.rows * (b ? 2.0 : 1.0) +
+                                                                       (scale ? m.rows : 0)));
+  launch(ex, m, SH_BT, x, EpiAxpy<T, 3>{b, scale, y, (T)alpha}, m.group);
+}
+
+// coarse dense inverse applied to NR right-hand sides: one warp per row
+template <int NR, class T>
+__global__ void k_dense(const T* __restrict__ M, int m, const T* __restrict__ b, T* __restrict__ y) {
+  int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  T acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = T(0);
+  for (int j = lane; j < m; j += 32) {
+    T a = M[(size_t)row * m + j];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] += a * b[(size_t)j * NR + r];
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  if (lane == 0)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) y[(size_t)row * NR + r] = acc[r];
+}
+
+template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y) {
+  ProfScope ps(ex, STOKES_KERNEL_OTHER, (double)sizeof(T) * ((double)m * m + 2.0 * m * nr));
+  int grid = cdiv(m, 8);
+  if (nr == 3) k_dense<3, T><<<grid, 256, 0, ex.s>>>(Minv, m, b, y);
+  else k_dense<1, T><<<grid, 256, 0, ex.s>>>(Minv, m, b, y);
+  SK_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time each group width on this matrix, keep the fastest
+// ---------------------------------------------------------------------------
+void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
+  if (m.rows == 0) return;
+  Shape sh = kind == 1 ? SH_BSR3 : kind == 2 ? SH_B : kind == 3 ? SH_BT : (nr == 3 ? SH_CSR3 : SH_CSR1);
+  int xin = (sh == SH_BSR3 || sh == SH_B) ? 3 : (sh == SH_BT ? 1 : nr);
+  int yout = (sh == SH_BSR3 || sh == SH_BT) ? 3 : (sh == SH_B ? 1 : nr);
+  bool f32 = m.v64 == nullptr;
+  size_t esz = f32 ? 4 : 8;
+  void *x = nullptr, *y = nullptr;
+  SK_CUDA(cudaMalloc(&x, esz * (size_t)m.cols * xin));
+  SK_CUDA(cudaMalloc(&y, esz * (size_t)m.rows * yout));
+  SK_CUDA(cudaMemsetAsync(x, 0, esz * (size_t)m.cols * xin, ex.s));
+  cudaEvent_t e0, e1;
+  SK_CUDA(cudaEventCreate(&e0));
+  SK_CUDA(cudaEventCreate(&e1));
+  Exec plain{ex.s, nullptr};
+  float best = FLT_MAX;
+  int bestg = m.group;
+  const int gs[5] = {2, 4, 8, 16, 32};
+  for (int gi = 0; gi < 5; ++gi) {
+    int g = gs[gi];
+    auto run = [&]() {
+      if (f32) {
+        if (yout == 3) launch(plain, m, sh, (const float*)x, EpiStore<float, 3>{(float*)y}, g);
+        else launch(plain, m, sh, (const float*)x, EpiStore<float, 1>{(float*)y}, g);
+      } else {
+        if (yout == 3) launch(plain, m, sh, (const double*)x, EpiStore<double, 3>{(double*)y}, g);
+        else launch(plain, m, sh, (const double*)x, EpiStore<double, 1>{(double*)y}, g);
+      }
+    };
+    run();
+    SK_CUDA(cudaEventRecord(e0, ex.s));
+    for (int rep = 0; rep < 5; ++rep) run();
+    SK_CUDA(cudaEventRecord(e1, ex.s));
+    SK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    SK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) best = ms, bestg = g;
+  }
+  m.group = bestg;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+}
+
+#define SK_INST(T)                                                                                        \
+  template void spmv_store<T>(const Exec&, const Csr&, int, const T*, T*, int);                          \
+  template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int);                            \
+  template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int);                \
+  template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
+                             double);                                                                     \
+  template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*);                          \
+  template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double);                     \
+  template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double);          \
+  template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*);
+SK_INST(float)
+SK_INST(double)
+
+}  // namespace sk

@@ -1,0 +1,111 @@
+"""GPU checks of the multigrid components.
+
+Transfers: on nested Kuhn meshes the coarse P2 (P1) space is contained in the
+fine one, so prolongation must reproduce any global quadratic (linear) field
+exactly at the fine nodes' logical positions, and restriction is its exact
+transpose. V-cycles: symmetric (so usable in CG) and contracting at a rate
+independent of h.
+"""
+
+import numpy as np
+import pytest
+
+import workload as wl
+from oracle.assemble import StokesSystem
+from oracle.mesh import KuhnMesh
+
+from gpu_helpers import cuda, gpu_module, host
+
+pytestmark = pytest.mark.gpu
+
+
+def logical_grid(n, interior_p2):
+    if interior_p2:
+        q = np.arange(1, 2 * n) / (2.0 * n)
+    else:
+        q = np.arange(n + 1) / float(n)
+    K, J, I = np.meshgrid(q, q, q, indexing="ij")
+    return np.stack([I.ravel(), J.ravel(), K.ravel()], 1)
+
+
+def quad_field(X, C):
+    x, y, z = X.T
+    mons = np.stack([np.ones_like(x), x, y, z, x * x, y * y, z * z, x * y, y * z, x * z])
+    return (C @ mons).T
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_prolongation_exact_on_polynomials(n):
+    """Coarse interior values of a quadratic q: the prolonged field equals q at every
+    fine node whose coarse cube has only interior nodes (boundary coarse values
+    are not unknowns, so elsewhere the interpolant differs from q)."""
+    sk = gpu_module()
+    S = sk.Stokes(n, wl.kuhn_vertices(n, 0.2, 1), 1.0, 0.01)
+    rng = np.random.default_rng(n)
+    C = rng.standard_normal((3, 10))
+    nc = n // 2
+    Xc = logical_grid(nc, True)
+    Xf = logical_grid(n, True)
+    ucoarse = quad_field(Xc, C)
+    y = host(S.apply("PROLONG_P2", cuda(ucoarse.ravel()), Xf.shape[0] * 3, level=0)).reshape(-1, 3)
+    ufine = quad_field(Xf, C)
+    inside = np.all((Xf > 1.0 / nc) & (Xf < 1.0 - 1.0 / nc), axis=1)
+    assert inside.sum() > 0
+    assert np.abs(y[inside] - ufine[inside]).max() < 1e-12 * np.abs(ufine).max()
+    # restriction is the transpose of prolongation
+    a = rng.standard_normal(Xc.shape[0] * 3)
+    b = rng.standard_normal(Xf.shape[0] * 3)
+    Pa = host(S.apply("PROLONG_P2", cuda(a), b.size, level=0))
+    Rb = host(S.apply("RESTRICT_P2", cuda(b), a.size, level=0))
+    assert abs(Pa @ b - a @ Rb) < 1e-12 * abs(Pa @ b)
+    # P1: linear fields are reproduced everywhere (all P1 nodes are unknowns)
+    Xc1 = logical_grid(nc, False)
+    Xf1 = logical_grid(n, False)
+    L = rng.standard_normal(4)
+    lin = lambda X: L[0] + X @ L[1:]  # noqa: E731
+    y1 = host(S.apply("PROLONG_P1", cuda(lin(Xc1)), Xf1.shape[0], level=0))
+    assert np.abs(y1 - lin(Xf1)).max() < 1e-12 * np.abs(lin(Xf1)).max()
+    S.close()
+
+
+def vcycle_stats(sk, n, mu, dt, which, seed=0):
+    V = wl.kuhn_vertices(n, 0.2, 2)
+    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(vcycles=1))
+    orc = StokesSystem(KuhnMesh(n, V), mu, dt)
+    rng = np.random.default_rng(seed)
+    if which == "A3":
+        A = orc.A3s
+        apply = lambda r: host(S.apply("VCYCLE_A3", cuda(r), r.size))  # noqa: E731
+        mat = lambda x: (A @ x.reshape(-1, 3)).ravel()  # noqa: E731
+        m = 3 * A.shape[0]
+    else:
+        A = (orc.MQ + orc.LQ).tocsr()
+        apply = lambda r: host(S.apply("VCYCLE_KQ", cuda(r), r.size))  # noqa: E731
+        mat = lambda x: A @ x  # noqa: E731
+        m = A.shape[0]
+    x = rng.standard_normal(m)
+    y = rng.standard_normal(m)
+    sym = abs(apply(x) @ y - x @ apply(y)) / abs(x @ apply(y))
+    # error propagation e <- (I - V A) e: contraction over 8 cycles
+    e = rng.standard_normal(m)
+    n0 = np.sqrt(e @ mat(e))
+    for _ in range(8):
+        e = e - apply(mat(e))
+    rate = (np.sqrt(e @ mat(e)) / n0) ** (1 / 8)
+    S.close()
+    return sym, rate
+
+
+@pytest.mark.parametrize("mu,dt", [(1.0, 1e-3), (1e-2, 1e-3), (1e-4, 1e-3), (1.0, 1.0)])
+def test_vcycle_symmetric_and_contracting(mu, dt):
+    sk = gpu_module()
+    rates = []
+    for n in (8, 16):
+        sym, rate = vcycle_stats(sk, n, mu, dt, "A3")
+        assert sym < 1e-10
+        assert rate < 0.5, (n, rate)
+        rates.append(rate)
+    assert rates[1] < rates[0] + 0.15        # no growth with refinement
+    for n in (8, 16):
+        sym, rate = vcycle_stats(sk, n, mu, dt, "KQ")
+        assert sym < 1e-10 and rate < 0.5
