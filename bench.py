@@ -220,9 +220,11 @@ def run_ours(args):
     dofs = 3 * (2 * n + 1) ** 3 + (n + 1) ** 3
     prec = sk.PRECISION_MIXED if args.precision == "mixed" else sk.PRECISION_FP64
 
+    mus = tuple(args.mus) if args.mus else MUS
+
     def make(precision, profile):
         solvers, fs, outs = [], [], []
-        for mu in MUS:
+        for mu in mus:
             opt = sk.stokes_default_options(precision=precision, profile=profile)
             S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
             f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
@@ -267,12 +269,12 @@ def run_ours(args):
     t_setup = time.perf_counter()
     solvers, fs, outs = make(prec, 1)
     torch.cuda.synchronize()
-    setup_s = (time.perf_counter() - t_setup) / len(MUS)
+    setup_s = (time.perf_counter() - t_setup) / len(mus)
     clocks = Clocks(local)
     ms, infos, ck = timed(solvers, fs, outs, args.steps, args.warmup, clocks)
     worst = max(i["rel_residual"] for i in infos)
     bad = [i for i in infos if i["status"] != 0]
-    value = world * len(MUS) * dofs / (ms / 1e3)
+    value = world * len(mus) * dofs / (ms / 1e3)
 
     # per-kernel CUDA-event statistics over the timed region
     kinfo = {}
@@ -309,7 +311,7 @@ def run_ours(args):
     uh = [torch.empty_like(f, device="cpu").pin_memory().numpy() for f in fs]
     ph = [torch.empty(S.n_p1, dtype=torch.float64).pin_memory().numpy() for S in solvers]
     e2e_ms = []
-    for it in range(args.warmup + args.steps):
+    for it in range(0 if args.no_e2e else args.warmup + args.steps):
         barrier()
         t0 = time.perf_counter()
         for S, f, u, p in zip(solvers, fh_np, uh, ph):
@@ -317,7 +319,7 @@ def run_ours(args):
         barrier()
         if it >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_step = statistics.mean(e2e_ms)
+    e2e_step = statistics.mean(e2e_ms) if e2e_ms else float("nan")
     if dist is not None:
         t = torch.tensor([e2e_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -332,7 +334,7 @@ def run_ours(args):
     if prec == sk.PRECISION_MIXED and not args.no_fp64:
         s2, f2, o2 = make(sk.PRECISION_FP64, 0)
         ms64, inf64, _ = timed(s2, f2, o2, max(1, args.steps // 2), max(1, args.warmup // 2))
-        fp64 = {"value": world * len(MUS) * dofs / (ms64 / 1e3), "ms_per_step": ms64,
+        fp64 = {"value": world * len(mus) * dofs / (ms64 / 1e3), "ms_per_step": ms64,
                 "worst_residual": max(i["rel_residual"] for i in inf64),
                 "iters": [(i["outer_iters"], i["inner_iters"], i["refinements"]) for i in inf64[:3]]}
         for S in s2:
@@ -340,15 +342,15 @@ def run_ours(args):
 
     if rank != 0:
         return None
-    cpu = run_cpu_baseline(1) if world == 1 else None
+    cpu = run_cpu_baseline(1) if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == sk.PRECISION_MIXED else "f64",
         "data": "synthetic (seeded jittered Kuhn mesh, manufactured solution)",
-        "config": config(n, args.precision),
+        "config": config(n, args.precision) if not args.mus else dict(config(n, args.precision), mus=list(mus)),
         "clocks": ck,
-        "e2e": {"value": world * len(MUS) * dofs / (e2e_step / 1e3), "unit": UNIT,
+        "e2e": {"value": world * len(mus) * dofs / (e2e_step / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": int(total_launches),
         "roofline": roofline,
@@ -402,6 +404,9 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--cpu-baseline-worker", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_worker:
