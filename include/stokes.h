@@ -171,6 +171,24 @@ typedef enum {
 
 stokes_status stokes_apply(stokes_ctx* ctx, int op, int level, const double* x, double* y);
 
+/* y = A x + gamma mu B^T M_Q^{-1} B x without allocating any device memory.
+ * The paper has no counterpart: this exists for callers that must not call
+ * cudaMalloc once they are running (a host loop that owns a fixed device
+ * memory budget, or code running while another framework owns the device
+ * allocator). Same arithmetic and result as stokes_apply(ctx,
+ * STOKES_OP_AGAMMA, 0, x, y); x and y are device arrays [(2n-1)^3][3] on the
+ * stream given to stokes_setup, and the call returns after that stream has
+ * finished the work.
+ * Work space: one fixed array of 4 x 2^20 doubles (32 MiB) that every GPU
+ * loading this library holds until the process exits. Meshes with more than
+ * 2^20 pressure nodes (n > 100) are rejected with STOKES_ERR_ARG. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture. All calls
+ * share the array and leave their data in it; the call overwrites every entry
+ * it reads, so nothing needs clearing, but calls whose kernels overlap on the
+ * GPU (other streams or threads at the same time) race on it. */
+stokes_status stokes_apply_agamma_noalloc(stokes_ctx* ctx, const double* x, double* y);
+
 /* Assembled matrices, for checks against an independent assembly. */
 typedef enum {
   STOKES_MAT_A = 0,    /* BSR 3x3, interior P2 x interior P2                 */

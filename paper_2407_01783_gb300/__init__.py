@@ -25,7 +25,7 @@ from ._lib import (KERNEL, MAT, METHOD_COUPLED, METHOD_SCHUR, OP, PRECISION_FP64
 
 __all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "stokes_default_options",
            "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_adjoint",
-           "stokes_destroy", "stokes_apply", "stokes_matrix_export", "stokes_sizes",
+           "stokes_destroy", "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_export", "stokes_sizes",
            "stokes_kernel_stats", "stokes_kernel_stats_reset", "StokesSolve", "OP", "MAT",
            "KERNEL", "METHOD_SCHUR", "METHOD_COUPLED", "SCHUR_PREC_LUMPED",
            "SCHUR_PREC_LAPLACE", "PRECISION_FP64", "PRECISION_MIXED", "library_path"]
@@ -120,6 +120,12 @@ def stokes_destroy(ctx):
 
 def stokes_apply(ctx, op: int, x: torch.Tensor, y: torch.Tensor, level: int = 0):
     _check(_L.stokes_apply(ctx, op, level, _ptr(x), _ptr(y)), "stokes_apply")
+    return y
+
+
+def stokes_apply_agamma_noalloc(ctx, x: torch.Tensor, y: torch.Tensor):
+    """A_gamma x through the allocation-free entry point (fixed work array)."""
+    _check(_L.stokes_apply_agamma_noalloc(ctx, _ptr(x), _ptr(y)), "stokes_apply_agamma_noalloc")
     return y
 
 

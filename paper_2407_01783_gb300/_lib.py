@@ -83,6 +83,8 @@ def load() -> C.CDLL:
     lib.stokes_last_error.restype = C.c_char_p
     lib.stokes_apply.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.stokes_apply.restype = C.c_int
+    lib.stokes_apply_agamma_noalloc.argtypes = [vp, vp, vp]
+    lib.stokes_apply_agamma_noalloc.restype = C.c_int
     lib.stokes_matrix_shape.argtypes = [vp, C.c_int, C.c_int, i64p]
     lib.stokes_matrix_shape.restype = C.c_int
     lib.stokes_matrix_export.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
@@ -101,5 +103,5 @@ def load() -> C.CDLL:
 # names declared in include/stokes.h (checked by the CPU test suite)
 EXPORTS = ["stokes_default_options", "stokes_setup", "stokes_solve", "stokes_solve_host",
            "stokes_adjoint", "stokes_destroy", "stokes_status_string", "stokes_last_error",
-           "stokes_apply", "stokes_matrix_shape", "stokes_matrix_export", "stokes_sizes",
+           "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_shape", "stokes_matrix_export", "stokes_sizes",
            "stokes_kernel_stats", "stokes_kernel_stats_reset"]

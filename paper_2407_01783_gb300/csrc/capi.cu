@@ -13,6 +13,7 @@
 namespace sk {
 
 static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 void* Arena::raw(size_t bytes) {
   void* p = nullptr;

@@ -299,5 +299,6 @@ int adjoint_context(stokes_ctx* c, const double* dJdu, const double* dJdp, doubl
 void apply_operator(stokes_ctx* c, int op, int level, const double* x, double* y);
 double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps, uint64_t seed);
 void set_breakdown_flag(int* f);
+void set_last_error(const std::string& msg);  // message returned by stokes_last_error()
 void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
 }  // namespace sk
