@@ -85,8 +85,16 @@ typedef struct {
   int max_outer;         /* outer Krylov iterations per refinement pass */
   int max_inner;         /* inner Krylov iterations per solve */
   int max_refine;        /* refinement passes on the full FP64 residual */
-  int profile;           /* 1: record per-kernel CUDA-event timings */
+  int profile;           /* 1: count launches and time every kernel class with CUDA
+                            events; 2 + k: count all, time only class k
+                            (STOKES_KERNEL_*); 0: off */
   int spmv_group;        /* threads per sparse row: 0 autotune, else 1..32 */
+  double pass_tol;       /* mixed precision: relative reduction asked of each FP32
+                            correction pass (outer Krylov tolerance per pass);
+                            its inner velocity solves get max(inner_tol,
+                            pass_tol/30). Default 3e-2. */
+  int format;            /* 0: stencil-structured storage where the mesh allows
+                            (A~_3, eps M_Q + L_Q, M_Q, L_Q), 1: CSR everywhere */
 } stokes_options;
 
 typedef struct {
@@ -145,8 +153,9 @@ const char* stokes_status_string(int status);
 const char* stokes_last_error(void);
 
 /* ---- operator access: building blocks of the solve, for tests and tools ----
- * Operators act on REDUCED vectors: velocity = interior P2 nodes
- * [(2n-1)^3][3] (interleaved), pressure = [(n+1)^3]. x and y are device
+ * Operators act on REDUCED vectors: velocity = interior P2 nodes stored
+ * component-major [3][(2n-1)^3] (the solver's internal layout: component c of
+ * interior node i at c*(2n-1)^3 + i), pressure = [(n+1)^3]. x and y are device
  * arrays of the operator's column / row length. `level` selects a multigrid
  * level (0 = the mesh given to setup) where it applies, else must be 0. */
 typedef enum {
@@ -166,7 +175,8 @@ typedef enum {
   STOKES_OP_PROLONG_P2 = 13,  /* y(level) = P x(level+1), 3 components         */
   STOKES_OP_RESTRICT_P2 = 14, /* y(level+1) = P^T x(level)                     */
   STOKES_OP_PROLONG_P1 = 15,  /* y(level) = P x(level+1)                       */
-  STOKES_OP_LOAD = 16         /* y = M_V f on interior rows, x = nodal f (all) */
+  STOKES_OP_LOAD = 16         /* y = M_V f on interior rows, x = nodal f on all
+                                 nodes [(2n+1)^3][3] (node-interleaved)       */
 } stokes_op;
 
 stokes_status stokes_apply(stokes_ctx* ctx, int op, int level, const double* x, double* y);
@@ -176,7 +186,7 @@ stokes_status stokes_apply(stokes_ctx* ctx, int op, int level, const double* x, 
  * cudaMalloc once they are running (a host loop that owns a fixed device
  * memory budget, or code running while another framework owns the device
  * allocator). Same arithmetic and result as stokes_apply(ctx,
- * STOKES_OP_AGAMMA, 0, x, y); x and y are device arrays [(2n-1)^3][3] on the
+ * STOKES_OP_AGAMMA, 0, x, y); x and y are device arrays [3][(2n-1)^3] on the
  * stream given to stokes_setup, and the call returns after that stream has
  * finished the work.
  * Work space: one fixed array of 4 x 2^20 doubles (32 MiB) that every GPU
@@ -228,6 +238,8 @@ typedef enum {
 stokes_status stokes_kernel_stats(stokes_ctx* ctx, int kernel, int64_t* launches,
                                   double* total_ms, double* bytes);
 stokes_status stokes_kernel_stats_reset(stokes_ctx* ctx);
+/* Change the profiling mode of a context (same values as options.profile). */
+stokes_status stokes_profile_mode(stokes_ctx* ctx, int mode);
 
 #ifdef __cplusplus
 }

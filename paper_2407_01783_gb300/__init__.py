@@ -26,7 +26,7 @@ from ._lib import (KERNEL, MAT, METHOD_COUPLED, METHOD_SCHUR, OP, PRECISION_FP64
 __all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "stokes_default_options",
            "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_adjoint",
            "stokes_destroy", "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_export", "stokes_sizes",
-           "stokes_kernel_stats", "stokes_kernel_stats_reset", "StokesSolve", "OP", "MAT",
+           "stokes_kernel_stats", "stokes_kernel_stats_reset", "stokes_profile_mode", "StokesSolve", "OP", "MAT",
            "KERNEL", "METHOD_SCHUR", "METHOD_COUPLED", "SCHUR_PREC_LUMPED",
            "SCHUR_PREC_LAPLACE", "PRECISION_FP64", "PRECISION_MIXED", "library_path"]
 
@@ -164,6 +164,10 @@ def stokes_kernel_stats(ctx, kernel: int):
 
 def stokes_kernel_stats_reset(ctx):
     _check(_L.stokes_kernel_stats_reset(ctx), "stokes_kernel_stats_reset")
+
+
+def stokes_profile_mode(ctx, mode: int):
+    _check(_L.stokes_profile_mode(ctx, mode), "stokes_profile_mode")
 
 
 class Stokes:

@@ -36,6 +36,7 @@ class StokesOptions(C.Structure):
         ("m2_inner_cg", C.c_int), ("inner_tol", C.c_double), ("schur_inner_tol", C.c_double),
         ("eps_pressure", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
         ("max_refine", C.c_int), ("profile", C.c_int), ("spmv_group", C.c_int),
+        ("pass_tol", C.c_double), ("format", C.c_int),
     ]
 
     def as_dict(self):
@@ -95,6 +96,8 @@ def load() -> C.CDLL:
     lib.stokes_kernel_stats.restype = C.c_int
     lib.stokes_kernel_stats_reset.argtypes = [vp]
     lib.stokes_kernel_stats_reset.restype = C.c_int
+    lib.stokes_profile_mode.argtypes = [vp, C.c_int]
+    lib.stokes_profile_mode.restype = C.c_int
     _ = ip
     _lib = lib
     return lib
@@ -104,4 +107,4 @@ def load() -> C.CDLL:
 EXPORTS = ["stokes_default_options", "stokes_setup", "stokes_solve", "stokes_solve_host",
            "stokes_adjoint", "stokes_destroy", "stokes_status_string", "stokes_last_error",
            "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_shape", "stokes_matrix_export", "stokes_sizes",
-           "stokes_kernel_stats", "stokes_kernel_stats_reset"]
+           "stokes_kernel_stats", "stokes_kernel_stats_reset", "stokes_profile_mode"]

@@ -80,7 +80,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     changed = any(c for _, c in results) or not os.path.exists(LIB)
     if changed:
         tmp = LIB + ".tmp"
-        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or res.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)

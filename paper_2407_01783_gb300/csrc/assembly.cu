@@ -53,6 +53,7 @@ static void ref_tet(int p, int v[4][3]) {
 struct StencilTables {
   int* d_off = nullptr;       // 3 ints per offset
   int beg[4][9];              // per pattern kind: offsets of class c in [beg[c], beg[c+1])
+  std::vector<int> h_off;     // host copy of the offsets
 };
 
 StencilTables* stencils_create(Arena& ar) {
@@ -91,6 +92,7 @@ StencilTables* stencils_create(Arena& ar) {
       for (const Off& o : sets[kind * 8 + c]) flat.insert(flat.end(), o.begin(), o.end());
       st->beg[kind][c + 1] = (int)(flat.size() / 3);
     }
+  st->h_off = flat;
   st->d_off = ar.alloc<int>(flat.size());
   SK_CUDA(cudaMemcpy(st->d_off, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice));
   upload_constants();
@@ -555,7 +557,8 @@ __global__ void __launch_bounds__(128) k_load(LoadArgs a) {
         double m = p2_mass420(ra, cb);
         for (int c = 0; c < 3; ++c) s[c] += m * fl[cb][c];
       }
-      for (int c = 0; c < 3; ++c) a.F[3 * (size_t)ri[ra] + c] += tg.vol * s[c] / 420.0;
+      const size_t nvi = (size_t)(2 * a.n - 1) * (2 * a.n - 1) * (2 * a.n - 1);
+      for (int c = 0; c < 3; ++c) a.F[c * nvi + ri[ra]] += tg.vol * s[c] / 420.0;  // component-major
     }
   }
 }
@@ -603,7 +606,8 @@ __global__ void __launch_bounds__(128) k_load_t(LoadArgs a) {
       local_node(tg, l, q);
       ri[l] = p2_interior_index(a.n, q);
       gid[l] = (size_t)q[0] + N * ((size_t)q[1] + (size_t)N * q[2]);
-      for (int c = 0; c < 3; ++c) ul[l][c] = ri[l] >= 0 ? a.f[3 * (size_t)ri[l] + c] : 0.0;
+      const size_t nvi = (size_t)(2 * a.n - 1) * (2 * a.n - 1) * (2 * a.n - 1);
+      for (int c = 0; c < 3; ++c) ul[l][c] = ri[l] >= 0 ? a.f[c * nvi + ri[l]] : 0.0;
     }
     for (int cb = 0; cb < 10; ++cb) {
       double s[3] = {0, 0, 0};
@@ -827,6 +831,100 @@ __global__ void k_diag_inv(int rows, const int* __restrict__ rp, const int* __re
 void diag_inverse(const Exec& ex, const Csr& m, double* dinv) {
   k_diag_inv<<<cdiv(m.rows, 256), 256, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, dinv);
   SK_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// stencil-structured storage (see StencilOp in internal.h)
+// ---------------------------------------------------------------------------
+StArgs stencil_args(const StencilOp& so, int block) {
+  StArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.p2 = so.p2;
+  a.n = so.n;
+  a.ncls = so.ncls;
+  a.lo = so.p2 ? 1 : 0;
+  a.hi = so.p2 ? 2 * so.n - 1 : 2 * so.n;
+  a.m = so.p2 ? 2 * so.n - 1 : so.n + 1;
+  int b = 0;
+  for (int c = 0; c < so.ncls; ++c) {
+    a.rows[c] = so.rows[c];
+    a.S[c] = so.S[c];
+    a.dbeg[c] = so.dbeg[c];
+    a.voff[c] = so.voff[c];
+    for (int k = 0; k < 3; ++k) a.ext[c][k] = so.ext[c][k], a.q0[c][k] = so.q0[c][k];
+    a.bbeg[c] = b;
+    b += cdiv(so.rows[c], block);
+  }
+  a.bbeg[so.ncls] = b;
+  for (int e = 0; e < so.nd; ++e) {
+    for (int k = 0; k < 3; ++k) a.d[e][k] = so.d[e][k];
+    a.lin[e] = so.lin[e];
+  }
+  return a;
+}
+
+__global__ void k_stencil_fill(const StArgs a, const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ out) {
+  int c, r;
+  if (!st_locate(a, c, r)) return;
+  int qx, qy, qz;
+  st_coords(a, c, r, qx, qy, qz);
+  const int row = st_index(a, qx, qy, qz);
+  const int lo = rp[row], hi = rp[row + 1];
+  for (int e = 0; e < a.S[c]; ++e) {
+    const int de = a.dbeg[c] + e;
+    const int nx = qx + a.d[de][0], ny = qy + a.d[de][1], nz = qz + a.d[de][2];
+    double w = 0.0;
+    if (st_inside(a, nx, ny, nz)) {
+      int pos = find_col(col, lo, hi, row + a.lin[de]);
+      if (pos >= 0) w = val[pos];
+    }
+    out[a.voff[c] + (size_t)e * a.rows[c] + r] = w;
+  }
+}
+
+StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int p2, int n, const Csr& m) {
+  SK_REQUIRE(m.br == 1 && m.bc == 1 && m.v64, STOKES_ERR_ARG, "stencil storage needs a scalar FP64 CSR matrix");
+  auto* so = new StencilOp();
+  so->p2 = p2;
+  so->n = n;
+  so->ncls = p2 ? 8 : 1;
+  const int kind = p2 ? PAT_P2P2 : PAT_P1P1;
+  const int mm = p2 ? 2 * n - 1 : n + 1;
+  long long off = 0;
+  int nd = 0;
+  for (int c = 0; c < so->ncls; ++c) {
+    for (int k = 0; k < 3; ++k) {
+      int par = p2 ? ((c >> k) & 1) : 0;
+      so->q0[c][k] = p2 ? (par ? 1 : 2) : 0;
+      so->ext[c][k] = p2 ? (par ? n : n - 1) : n + 1;
+    }
+    so->rows[c] = so->ext[c][0] * so->ext[c][1] * so->ext[c][2];
+    so->dbeg[c] = nd;
+    for (int e = st->beg[kind][c]; e < st->beg[kind][c + 1]; ++e) {
+      SK_REQUIRE(nd < kMaxStencil, STOKES_ERR_ARG, "stencil table overflow");
+      int dx = st->h_off[3 * e], dy = st->h_off[3 * e + 1], dz = st->h_off[3 * e + 2];
+      so->d[nd][0] = (signed char)dx;
+      so->d[nd][1] = (signed char)dy;
+      so->d[nd][2] = (signed char)dz;
+      so->lin[nd] = p2 ? dx + mm * (dy + mm * dz) : dx / 2 + mm * (dy / 2 + mm * (dz / 2));
+      ++nd;
+    }
+    so->S[c] = nd - so->dbeg[c];
+    so->voff[c] = off;
+    off += (long long)so->S[c] * so->rows[c];
+  }
+  so->nd = nd;
+  so->total = off;
+  long long rows_all = 0;
+  for (int c = 0; c < so->ncls; ++c) rows_all += so->rows[c];
+  SK_REQUIRE(off < (1LL << 32) && 3 * rows_all < (1LL << 32), STOKES_ERR_ARG,
+             "stencil storage needs 32-bit indices (mesh too large)");
+  so->v64 = ar.alloc<double>(off);
+  StArgs a = stencil_args(*so, 128);
+  k_stencil_fill<<<a.bbeg[so->ncls], 128, 0, ex.s>>>(a, m.rowptr, m.col, m.v64, so->v64);
+  SK_CHECK_LAUNCH();
+  return so;
 }
 
 __global__ void k_to_f32(const double* __restrict__ s, float* __restrict__ d, size_t n) {

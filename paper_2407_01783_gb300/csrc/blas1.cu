@@ -19,34 +19,55 @@ template <class T> struct DotArgs {
   const T* x[kMaxDots];
   const T* y[kMaxDots];
   int k;
+  int compensated;  // FP32 inputs: per-thread Neumaier sums in FP32, FP64 across threads
   size_t n;
   double* partial;
   unsigned* counter;
   double* out;
 };
 
-template <class T>
+template <class T, int K>
 __global__ void __launch_bounds__(256) k_dots(DotArgs<T> a) {
-  double s[kMaxDots];
+  double s[K];
 #pragma unroll
-  for (int j = 0; j < kMaxDots; ++j) s[j] = 0.0;
+  for (int j = 0; j < K; ++j) s[j] = 0.0;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+  if (a.compensated) {
+    // GB300 runs FP64 at a small fraction of its FP32 rate, so products and
+    // per-thread sums of FP32 vectors stay in FP32 with Neumaier's compensated
+    // summation (error ~ eps_32 per product, not per partial sum); only the
+    // cross-thread reduction is FP64.
+    float fs[K], fc[K];
 #pragma unroll
-    for (int j = 0; j < kMaxDots; ++j)
-      if (j < a.k) s[j] += (double)a.x[j][i] * (a.y[j] ? (double)a.y[j][i] : 1.0);
+    for (int j = 0; j < K; ++j) fs[j] = 0.f, fc[j] = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        float p = (float)a.x[j][i] * (a.y[j] ? (float)a.y[j][i] : 1.f);
+        float t = fs[j] + p;
+        fc[j] += fabsf(fs[j]) >= fabsf(p) ? (fs[j] - t) + p : (p - t) + fs[j];
+        fs[j] = t;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) s[j] = (double)fs[j] + (double)fc[j];
+  } else {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) s[j] += (double)a.x[j][i] * (a.y[j] ? (double)a.y[j][i] : 1.0);
+    }
   }
-  __shared__ double sh[kMaxDots][8];
+  __shared__ double sh[K][8];
   __shared__ bool last;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < kMaxDots; ++j) {
+  for (int j = 0; j < K; ++j) {
     double v = s[j];
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) sh[j][wid] = v;
   }
   __syncthreads();
-  if (threadIdx.x < kMaxDots) {
+  if (threadIdx.x < K) {
     double v = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
     a.partial[threadIdx.x * gridDim.x + blockIdx.x] = v;
@@ -57,7 +78,7 @@ __global__ void __launch_bounds__(256) k_dots(DotArgs<T> a) {
   __syncthreads();
   if (!last) return;
   // the last block: fixed-order sum of the partials
-  for (int j = 0; j < a.k; ++j) {
+  for (int j = 0; j < K; ++j) {
     double v = 0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(&a.partial[j * gridDim.x + b]);
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -81,11 +102,17 @@ void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const 
   for (int j = 0; j < k; ++j) a.x[j] = x[j], a.y[j] = y ? y[j] : nullptr;
   a.k = k;
   a.n = n;
+  a.compensated = std::is_same<T, float>::value && n >= kCompensatedMin;
   a.partial = ds.partial;
   a.counter = ds.counter;
   a.out = out;
   int grid = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, cdiv((long long)n, 256)));
-  k_dots<T><<<grid, 256, 0, ex.s>>>(a);
+  switch (k) {
+    case 1: k_dots<T, 1><<<grid, 256, 0, ex.s>>>(a); break;
+    case 2: k_dots<T, 2><<<grid, 256, 0, ex.s>>>(a); break;
+    case 3: k_dots<T, 3><<<grid, 256, 0, ex.s>>>(a); break;
+    default: k_dots<T, 4><<<grid, 256, 0, ex.s>>>(a); break;
+  }
   SK_CHECK_LAUNCH();
 }
 
@@ -94,10 +121,22 @@ void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const 
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; \
   if (i >= n) return;
 
+// Coefficients from device scalars are evaluated once per block (one FP64
+// division per block instead of per element: GB300's FP64 rate is low).
+#define SK_COEF2(A, B, va, vb)                                  \
+  __shared__ double sk_coef_[2];                                \
+  if (threadIdx.x == 0) {                                       \
+    sk_coef_[0] = coef_value(A);                                \
+    sk_coef_[1] = coef_value(B);                                \
+  }                                                             \
+  __syncthreads();                                              \
+  const double va = sk_coef_[0], vb = sk_coef_[1];
+
 template <class T>
 __global__ void k_axpby(size_t n, Coef a, const T* __restrict__ x, Coef b, T* __restrict__ y) {
+  SK_COEF2(a, b, ad, bd);
   SK_IDX;
-  T av = (T)coef_value(a), bv = (T)coef_value(b);
+  const T av = (T)ad, bv = (T)bd;
   y[i] = av * x[i] + (bv == T(0) ? T(0) : bv * y[i]);
 }
 template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y) {
@@ -110,11 +149,13 @@ template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef
 template <class T>
 __global__ void k_cg_update(size_t n, Coef a, const T* __restrict__ d, T* __restrict__ x, const T* __restrict__ q,
                             T* __restrict__ r, int* flag) {
+  SK_COEF2(a, a, ad, unused);
+  (void)unused;
   SK_IDX;
-  double av = coef_value(a);
   if (i == 0 && a.den && !(*a.den > 0.0)) atomicOr(flag, 1);  // p^T A p <= 0: breakdown
-  x[i] += (T)av * d[i];
-  if (r) r[i] -= (T)av * q[i];
+  const T av = (T)ad;
+  x[i] += av * d[i];
+  if (r) r[i] -= av * q[i];
 }
 static int* g_flag = nullptr;  // set by the context before solves
 void set_breakdown_flag(int* f) { g_flag = f; }
@@ -126,8 +167,10 @@ template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, 
 }
 
 template <class T> __global__ void k_scale_copy(size_t n, Coef a, const T* __restrict__ x, T* __restrict__ y) {
+  SK_COEF2(a, a, ad, unused);
+  (void)unused;
   SK_IDX;
-  y[i] = (T)coef_value(a) * x[i];
+  y[i] = (T)ad * x[i];
 }
 template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x, T* y) {
   if (!n) return;
@@ -149,8 +192,11 @@ template <class T> void lincomb2(const Exec& ex, size_t n, double c1, const T* x
 }
 
 template <class T> __global__ void k_sub_ratio(size_t n, const double* num, const double* den, double scale, T* x) {
+  __shared__ double sk_v;
+  if (threadIdx.x == 0) sk_v = scale * (*num) / (den ? *den : 1.0);
+  __syncthreads();
   SK_IDX;
-  x[i] -= (T)(scale * (*num) / (den ? *den : 1.0));
+  x[i] -= (T)sk_v;
 }
 template <class T> void sub_mean(const Exec& ex, size_t n, const double* sum, double count, T* r) {
   if (!n) return;
@@ -166,17 +212,17 @@ template <class T> void sub_ratio(const Exec& ex, size_t n, const double* num, c
 }
 
 template <class T>
-__global__ void k_cheb_first(size_t n, int nr, const T* __restrict__ dinv, const T* __restrict__ b, T c,
+__global__ void k_cheb_first(size_t n, size_t rows, const T* __restrict__ dinv, const T* __restrict__ b, T c,
                              T* __restrict__ d, T* __restrict__ x) {
   SK_IDX;
-  T v = c * dinv[i / nr] * b[i];
+  T v = c * dinv[i % rows] * b[i];  // component-major: row of entry i is i mod rows
   d[i] = v;
   x[i] = v;
 }
 template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* dinv, const T* b, double c, T* d, T* x) {
   if (!n) return;
   ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * (n * 3 + n / nr));
-  k_cheb_first<T><<<SK_GRID(n)>>>(n, nr, dinv, b, (T)c, d, x);
+  k_cheb_first<T><<<SK_GRID(n)>>>(n, n / nr, dinv, b, (T)c, d, x);
   SK_CHECK_LAUNCH();
 }
 
@@ -210,7 +256,8 @@ __global__ void k_expand(int n, const double* __restrict__ ured, double* __restr
   int qx = (int)(i % N), qy = (int)((i / N) % N), qz = (int)(i / ((size_t)N * N));
   bool in = qx > 0 && qx < N - 1 && qy > 0 && qy < N - 1 && qz > 0 && qz < N - 1;
   size_t r = in ? (size_t)(qx - 1) + (size_t)m * ((qy - 1) + (size_t)m * (qz - 1)) : 0;
-  for (int c = 0; c < 3; ++c) uall[3 * i + c] = in ? ured[3 * r + c] : 0.0;
+  const size_t nvi = (size_t)m * m * m;
+  for (int c = 0; c < 3; ++c) uall[3 * i + c] = in ? ured[c * nvi + r] : 0.0;
 }
 void expand_velocity(const Exec& ex, int n, const double* ured, double* uall) {
   size_t tot = (size_t)(2 * n + 1) * (2 * n + 1) * (2 * n + 1);
@@ -225,7 +272,7 @@ __global__ void k_restrict_vel(int n, const double* __restrict__ uall, double* _
   if (r >= tot) return;
   int ix = (int)(r % m) + 1, iy = (int)((r / m) % m) + 1, iz = (int)(r / ((size_t)m * m)) + 1;
   size_t g = (size_t)ix + (size_t)N * (iy + (size_t)N * iz);
-  for (int c = 0; c < 3; ++c) ured[3 * r + c] = uall[3 * g + c];
+  for (int c = 0; c < 3; ++c) ured[c * tot + r] = uall[3 * g + c];
 }
 void restrict_velocity(const Exec& ex, int n, const double* uall, double* ured) {
   size_t tot = (size_t)(2 * n - 1) * (2 * n - 1) * (2 * n - 1);

@@ -103,6 +103,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   c.n = n;
   c.ex.prof = &c.prof;
   c.prof.on = c.opt.profile != 0;
+  c.prof.only = c.opt.profile >= 2 ? c.opt.profile - 2 : -1;
   c.pool.arena = &c.arena;
   c.mixed = c.opt.precision == STOKES_PRECISION_MIXED;
   c.sc.cap = 1024;
@@ -188,6 +189,19 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     build_transfer_p2(c.ex, c.arena, c.lv[l].n, c.lv[l + 1].n, c.lv[l].P2, c.lv[l].R2);
     build_transfer_p1(c.ex, c.arena, c.lv[l].n, c.lv[l + 1].n, c.lv[l].P1, c.lv[l].R1);
   }
+  if (c.opt.format == 0) {
+    auto add = [&](Csr& m, int p2, int nn) {
+      if (m.rows < kStencilMinRows) return;
+      c.stencils.emplace_back(stencil_from_csr(c.ex, c.arena, st, p2, nn, m));
+      m.st = c.stencils.back().get();
+    };
+    for (Level& L : c.lv) {
+      add(L.A3, 1, L.n);
+      add(L.KQ, 0, L.n);
+    }
+    add(c.MQ, 0, n);
+    add(c.LQ, 0, n);
+  }
   Level& Lc = c.lv.back();
   coarse_inverse(c, Lc.A3, &Lc.A3_cinv64);
   coarse_inverse(c, Lc.KQ, &Lc.KQ_cinv64);
@@ -236,6 +250,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
       for (Csr* t : {&L.P2, &L.R2, &L.P1, &L.R1})
         if (t->v64) t->v32 = f32_copy(c, t->v64, t->nnz);
     }
+    for (auto& so : c.stencils) so->v32 = f32_copy(c, so->v64, so->total);
     Lc.A3_cinv32 = f32_copy(c, Lc.A3_cinv64, (size_t)Lc.A3.rows * Lc.A3.rows);
     Lc.KQ_cinv32 = f32_copy(c, Lc.KQ_cinv64, (size_t)Lc.KQ.rows * Lc.KQ.rows);
   }
@@ -313,6 +328,8 @@ void stokes_default_options(stokes_options* o) {
   o->max_refine = 6;
   o->profile = 0;
   o->spmv_group = 0;
+  o->pass_tol = 3e-2;
+  o->format = 0;
 }
 
 const char* stokes_status_string(int s) {
@@ -346,7 +363,8 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
   if (!c) return STOKES_ERR_OOM;
   if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
   if (c->opt.vcycles < 1 || c->opt.cheb_degree < 1 || c->opt.restart < 2 || !(c->opt.eps_pressure > 0) ||
-      !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0)) {
+      !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 1 ||
+      !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1)) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;
@@ -545,6 +563,16 @@ stokes_status stokes_kernel_stats_reset(stokes_ctx* c) {
   return (stokes_status)guarded([&]() {
     SK_CUDA(cudaStreamSynchronize(c->ex.s));
     c->prof.reset();
+  });
+}
+
+stokes_status stokes_profile_mode(stokes_ctx* c, int mode) {
+  if (!c || mode < 0 || mode >= 2 + STOKES_KERNEL_COUNT) return STOKES_ERR_ARG;
+  return (stokes_status)guarded([&]() {
+    SK_CUDA(cudaStreamSynchronize(c->ex.s));
+    c->opt.profile = mode;
+    c->prof.on = mode != 0;
+    c->prof.only = mode >= 2 ? mode - 2 : -1;
   });
 }
 

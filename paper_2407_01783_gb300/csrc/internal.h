@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
@@ -45,6 +46,7 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------
 struct Prof {
   bool on = false;
+  int only = -1;  // >= 0: CUDA events only around launches of this class (all are counted)
   struct Rec {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     double bytes = 0;
@@ -71,6 +73,70 @@ struct ProfScope {
 };
 
 // ---------------------------------------------------------------------------
+// Stencil-structured storage of a matrix on a Kuhn level. Every row node's
+// neighbours follow one of 8 fixed stencils (by the parity class of its
+// half-grid coordinates; P1 nodes have a single class), so a row needs no
+// column indices: column = row + lin[e] for stencil entry e when the neighbour
+// lies inside the index space, else the entry is absent (stored as 0). Values
+// of class c are stored [e][row-in-class] so that a warp of consecutive
+// same-class rows reads 128 contiguous bytes per entry.
+// ---------------------------------------------------------------------------
+constexpr int kMaxStencil = 256;
+struct StencilOp {
+  int p2 = 1;                // 1: interior P2 index space, 0: P1 index space
+  int n = 0;
+  int ncls = 0;
+  int rows[8] = {}, ext[8][3] = {}, q0[8][3] = {}, S[8] = {}, dbeg[8] = {};
+  long long voff[8] = {};
+  long long total = 0;       // stored entries (all classes)
+  signed char d[kMaxStencil][3] = {};  // half-grid offsets of entry e
+  int lin[kMaxStencil] = {};           // linear index offsets of entry e
+  int nd = 0;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  template <class T> T* v() const;
+};
+template <> inline double* StencilOp::v<double>() const { return v64; }
+template <> inline float* StencilOp::v<float>() const { return v32; }
+
+// Kernel-side view of a StencilOp (passed by value; blocks of one class are
+// contiguous: class c owns blocks [bbeg[c], bbeg[c+1])).
+struct StArgs {
+  int p2, n, ncls, lo, hi, m;
+  int rows[8], ext[8][3], q0[8][3], S[8], dbeg[8];
+  long long voff[8];
+  int bbeg[9];
+  signed char d[kMaxStencil][3];
+  int lin[kMaxStencil];
+};
+StArgs stencil_args(const StencilOp& s, int block);
+
+#ifdef __CUDACC__
+// class and row-in-class of this thread; false if past the class end
+__device__ __forceinline__ bool st_locate(const StArgs& a, int& c, int& r) {
+  c = 0;
+#pragma unroll 1
+  while (c + 1 < a.ncls && (int)blockIdx.x >= a.bbeg[c + 1]) ++c;
+  r = ((int)blockIdx.x - a.bbeg[c]) * (int)blockDim.x + (int)threadIdx.x;
+  return r < a.rows[c];
+}
+__device__ __forceinline__ void st_coords(const StArgs& a, int c, int r, int& qx, int& qy, int& qz) {
+  const int ex = a.ext[c][0], ey = a.ext[c][1];
+  qx = a.q0[c][0] + 2 * (r % ex);
+  qy = a.q0[c][1] + 2 * ((r / ex) % ey);
+  qz = a.q0[c][2] + 2 * (r / (ex * ey));
+}
+// index of half-grid node q in the matrix's index space
+__device__ __forceinline__ int st_index(const StArgs& a, int qx, int qy, int qz) {
+  if (a.p2) return (qx - 1) + a.m * ((qy - 1) + a.m * (qz - 1));
+  return (qx >> 1) + a.m * ((qy >> 1) + a.m * (qz >> 1));
+}
+__device__ __forceinline__ bool st_inside(const StArgs& a, int qx, int qy, int qz) {
+  return qx >= a.lo && qx <= a.hi && qy >= a.lo && qy <= a.hi && qz >= a.lo && qz <= a.hi;
+}
+#endif
+
+// ---------------------------------------------------------------------------
 // sparse matrices: CSR over (possibly) small dense blocks, values stored as
 // br*bc planes of nnz entries each (plane j at v + j*nnz) so that consecutive
 // lanes read consecutive addresses.
@@ -84,6 +150,7 @@ struct Csr {
   double* v64 = nullptr;
   float* v32 = nullptr;
   int group = 8;  // threads per row
+  const StencilOp* st = nullptr;  // same matrix in stencil storage (used when set)
   template <class T> T* v() const;
   double bytes(int elem) const {  // algorithmic bytes of one product (matrix only)
     return (double)nnz * (4.0 + elem * br * bc) + 4.0 * (rows + 1);
@@ -194,6 +261,9 @@ void assemble_load_transpose(const Exec& ex, int n, const double* X, const doubl
 void build_transfer_p2(const Exec& ex, Arena& ar, int nf, int nc, Csr& P, Csr& R);
 void build_transfer_p1(const Exec& ex, Arena& ar, int nf, int nc, Csr& P, Csr& R);
 void diag_inverse(const Exec& ex, const Csr& m, double* dinv);
+// Stencil storage of a square P2-interior (p2 = 1) or P1 (p2 = 0) matrix of
+// level size n, values copied from the assembled CSR m (FP64; FP32 on request).
+StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int p2, int n, const Csr& m);
 void to_f32(const Exec& ex, const double* src, float* dst, size_t n);
 void subsample_vertices(int n, const double* Xf_host, double* Xc_host);
 
@@ -229,6 +299,13 @@ struct DotScratch {
 };
 constexpr int kMaxDots = 4;
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+// FP32 vectors at least this long use compensated FP32 per-thread sums in
+// dots() (velocity-sized vectors of the inner solves); shorter ones
+// (pressure-sized, the outer Schur iteration) accumulate in FP64 throughout.
+constexpr size_t kCompensatedMin = (size_t)1 << 20;
+// Stencil storage is used on levels with at least this many rows; smaller
+// grids are latency-bound with one thread per row and stay CSR.
+constexpr int kStencilMinRows = 1 << 18;
 // out[i] = sum_j x_i[j] * y_i[j] for i < k (y_i == nullptr means all ones).
 template <class T> void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x,
                              const T* const* y, size_t n, double* out);
@@ -279,6 +356,7 @@ struct stokes_ctx {
   double MQ1_sum = 0;
   bool mixed = false;
   // last forward solution (reduced) for the adjoint
+  std::vector<std::unique_ptr<sk::StencilOp>> stencils;  // owned stencil storages
   double* U_last = nullptr;
   double* P_last = nullptr;
   bool have_solution = false;

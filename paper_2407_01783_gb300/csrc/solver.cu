@@ -587,8 +587,11 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
         break;
       }
       if (c.mixed) {
-        // FP32 inner work: one pass gains ~4 digits
-        double eta = std::max(1e-4, 0.5 * tol / rel), tin = std::max(c.opt.inner_tol, 1e-5);
+        // FP32 inner work: each pass asks for a reduction of pass_tol and its inner
+        // velocity solves for pass_tol / 30 (measured best on the 48^3 workload:
+        // cheap passes, about three of them to reach 1e-8)
+        double eta = std::max(c.opt.pass_tol, 0.5 * tol / rel);
+        double tin = std::max(c.opt.inner_tol, c.opt.pass_tol / 30.0);
         correction<float>(c, rF, rg, U, P, eta, tin);
       } else {
         double eta = std::max(0.5 * tol / rel, 1e-13);

@@ -36,6 +36,16 @@ def rel_err(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def soa(x):
+    """Node-interleaved [node][3] -> component-major [3][node] (the C ABI's reduced layout)."""
+    return np.ascontiguousarray(np.asarray(x).reshape(-1, 3).T).ravel()
+
+
+def aos(x):
+    """Component-major [3][node] -> node-interleaved [node][3]."""
+    return np.ascontiguousarray(np.asarray(x).reshape(3, -1).T).ravel()
+
+
 def cuda(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 

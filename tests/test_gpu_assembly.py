@@ -12,7 +12,7 @@ import workload as wl
 from oracle.assemble import StokesSystem
 from oracle.mesh import KuhnMesh
 
-from gpu_helpers import coarse_vertices, cuda, gpu_module, host, rel_err, to_scipy
+from gpu_helpers import aos, coarse_vertices, cuda, gpu_module, host, rel_err, soa, to_scipy
 
 pytestmark = pytest.mark.gpu
 
@@ -92,17 +92,18 @@ def test_operator_products(pair):
     nv, np_ = orc.A.shape[0], orc.B.shape[0]
     x = rng.standard_normal(nv)
     p = rng.standard_normal(np_)
-    assert rel_err(host(S.apply("A", cuda(x), nv)), orc.A @ x) < 1e-13
-    assert rel_err(host(S.apply("A3", cuda(x), nv)), (orc.A3s @ x.reshape(-1, 3)).ravel()) < 1e-13
-    assert rel_err(host(S.apply("B", cuda(x), np_)), orc.B @ x) < 1e-13
-    assert rel_err(host(S.apply("BT", cuda(p), nv)), orc.B.T @ p) < 1e-13
+    xs = cuda(soa(x))
+    assert rel_err(aos(host(S.apply("A", xs, nv))), orc.A @ x) < 1e-13
+    assert rel_err(aos(host(S.apply("A3", xs, nv))), (orc.A3s @ x.reshape(-1, 3)).ravel()) < 1e-13
+    assert rel_err(host(S.apply("B", xs, np_)), orc.B @ x) < 1e-13
+    assert rel_err(aos(host(S.apply("BT", cuda(p), nv))), orc.B.T @ p) < 1e-13
     assert rel_err(host(S.apply("MQ", cuda(p), np_)), orc.MQ @ p) < 1e-13
     assert rel_err(host(S.apply("LQ", cuda(p), np_)), orc.LQ @ p) < 1e-13
     assert rel_err(host(S.apply("KQ", cuda(p), np_)), (orc.MQ + orc.LQ) @ p) < 1e-13
-    assert rel_err(host(S.apply("LUMPED_INV", cuda(x), nv)), x / orc.Lam) < 1e-14
+    assert rel_err(aos(host(S.apply("LUMPED_INV", xs, nv))), x / orc.Lam) < 1e-14
     # load vector F = M_V f on interior rows from nodal f on all nodes
     f = rng.standard_normal((orc.mesh.n_p2, 3))
-    assert rel_err(host(S.apply("LOAD", cuda(f), nv)), orc.load(f)) < 1e-13
+    assert rel_err(aos(host(S.apply("LOAD", cuda(f), nv))), orc.load(f)) < 1e-13
 
 
 def test_augmented_operator_matches_definition():
@@ -117,5 +118,5 @@ def test_augmented_operator_matches_definition():
     x = rng.standard_normal(orc.A.shape[0])
     import scipy.sparse.linalg as spla
     ref = orc.A @ x + gamma * 0.5 * (orc.B.T @ spla.spsolve(orc.MQ.tocsc(), orc.B @ x))
-    assert rel_err(host(S.apply("AGAMMA", cuda(x), x.size)), ref) < 1e-8
+    assert rel_err(aos(host(S.apply("AGAMMA", cuda(soa(x)), x.size))), ref) < 1e-8
     S.close()

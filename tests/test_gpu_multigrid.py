@@ -14,7 +14,7 @@ import workload as wl
 from oracle.assemble import StokesSystem
 from oracle.mesh import KuhnMesh
 
-from gpu_helpers import cuda, gpu_module, host
+from gpu_helpers import aos, cuda, gpu_module, host, soa
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,7 @@ def test_prolongation_exact_on_polynomials(n):
     Xc = logical_grid(nc, True)
     Xf = logical_grid(n, True)
     ucoarse = quad_field(Xc, C)
-    y = host(S.apply("PROLONG_P2", cuda(ucoarse.ravel()), Xf.shape[0] * 3, level=0)).reshape(-1, 3)
+    y = aos(host(S.apply("PROLONG_P2", cuda(soa(ucoarse)), Xf.shape[0] * 3, level=0))).reshape(-1, 3)
     ufine = quad_field(Xf, C)
     inside = np.all((Xf > 1.0 / nc) & (Xf < 1.0 - 1.0 / nc), axis=1)
     assert inside.sum() > 0
@@ -76,7 +76,7 @@ def vcycle_stats(sk, n, mu, dt, which, seed=0):
     if which == "A3":
         A = orc.A3s
         apply = lambda r: host(S.apply("VCYCLE_A3", cuda(r), r.size))  # noqa: E731
-        mat = lambda x: (A @ x.reshape(-1, 3)).ravel()  # noqa: E731
+        mat = lambda x: soa((A @ aos(x).reshape(-1, 3)).ravel())  # noqa: E731
         m = 3 * A.shape[0]
     else:
         A = (orc.MQ + orc.LQ).tocsr()
