@@ -223,10 +223,10 @@ def run_ours(args):
 
     mus = tuple(args.mus) if args.mus else MUS
 
-    def make(precision, profile):
+    def make(precision, profile, **extra):
         solvers, fs, outs = [], [], []
         for mu in mus:
-            opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles)
+            opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles, **extra)
             S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
             f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
             u = torch.empty_like(f)
@@ -355,6 +355,17 @@ def run_ours(args):
         for S in s2:
             S.close()
 
+    coupled = None
+    if not args.no_coupled:
+        s3, f3, o3 = make(prec, 0, method=sk.METHOD_COUPLED, block_lu=1)
+        ms2, inf2, _ = timed(s3, f3, o3, max(1, args.steps // 2), max(1, args.warmup // 2))
+        coupled = {"value": world * len(mus) * dofs / (ms2 / 1e3), "ms_per_step": ms2,
+                   "method": "coupled FGMRES(30), block-LU preconditioner, V-cycles for A~^{-1}",
+                   "worst_residual": max(i["rel_residual"] for i in inf2),
+                   "iters": [(i["outer_iters"], i["refinements"]) for i in inf2[:len(mus)]]}
+        for S in s3:
+            S.close()
+
     if rank != 0:
         return None
     cpu = run_cpu_baseline(1) if (world == 1 and not args.no_cpu) else None
@@ -376,6 +387,7 @@ def run_ours(args):
         "iters": [(i["outer_iters"], i["inner_iters"], i["refinements"]) for i in infos[:3]],
         "kernels": kernels,
         "plain_fp64": fp64,
+        "method2_coupled": coupled,
     }
     return line
 
@@ -421,6 +433,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-coupled", action="store_true", help="skip the Method 2 (coupled FGMRES) line")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
     ap.add_argument("--cpu-baseline-worker", type=int, default=0, help=argparse.SUPPRESS)

@@ -225,7 +225,7 @@ stokes_status stokes_sizes(stokes_ctx* ctx, int64_t sizes[6]);
  * Returns launches, summed CUDA-event milliseconds and algorithmic bytes
  * (matrix read once, each vector read/written once) since the last reset. */
 typedef enum {
-  STOKES_KERNEL_SPMM_A3 = 0,      /* scalar CSR x 3 RHS (smoother/residual) */
+  STOKES_KERNEL_SPMM_A3 = 0,      /* A~_3 x 3 RHS on the finest level (smoother/residual) */
   STOKES_KERNEL_SPMV_A = 1,       /* BSR3 strain-form A                     */
   STOKES_KERNEL_B = 2,            /* divergence B                           */
   STOKES_KERNEL_BT = 3,           /* gradient B^T                           */
@@ -233,7 +233,9 @@ typedef enum {
   STOKES_KERNEL_TRANSFER = 5,     /* prolongation / restriction             */
   STOKES_KERNEL_BLAS1 = 6,        /* dots, axpys, projections               */
   STOKES_KERNEL_OTHER = 7,        /* load vectors, coarse solves, layouts   */
-  STOKES_KERNEL_COUNT = 8
+  STOKES_KERNEL_SPMM_A3_COARSE = 8, /* A~_3 x 3 RHS on the coarser levels   */
+  STOKES_KERNEL_RESIDUAL = 9,     /* A U in the FP64 full-system residual    */
+  STOKES_KERNEL_COUNT = 10
 } stokes_kernel;
 stokes_status stokes_kernel_stats(stokes_ctx* ctx, int kernel, int64_t* launches,
                                   double* total_ms, double* bytes);

@@ -278,9 +278,10 @@ template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T
 template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind);
 // Chebyshev step: r = b - A xin; d = c1 d + c2 dinv r; xout = xin + d.
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin,
-                                  T* d, T* xout, const T* dinv, double c1, double c2);
+                                  T* d, T* xout, const T* dinv, double c1, double c2, int kind);
 // BSR3 strain-form A: y = A x or y = b - A x (b may be null).
-template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b);
+template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b,
+                                   int kind = STOKES_KERNEL_SPMV_A);
 // B (1x3 blocks): y = B x;  B^T (3x1 blocks): y = B^T x, optionally scaled per row
 // (y_i = s_i * (B^T x)_i) and / or subtracted from b (y = b - ...) or added into y.
 template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha);

@@ -87,7 +87,8 @@ extern "C" stokes_status stokes_apply_agamma_noalloc(stokes_ctx* c, const double
       cheb_first<double>(ex, np, 1, c->MQ_dinv64, bx, 1.0 / theta, d, xa);
       for (int k = 1; k < steps; ++k) {
         double rn = 1.0 / (2.0 * sigma - rho);
-        spmv_cheb<double>(ex, c->MQ, 1, bx, xa, d, xb, c->MQ_dinv64, rn * rho, 2.0 * rn / delta);
+        spmv_cheb<double>(ex, c->MQ, 1, bx, xa, d, xb, c->MQ_dinv64, rn * rho, 2.0 * rn / delta,
+                          STOKES_KERNEL_SPMV_P1);
         double* t = xa;
         xa = xb;
         xb = t;

@@ -73,7 +73,7 @@ static size_t npres(const stokes_ctx& c) { return (size_t)c.lv[0].np; }
 // ---------------------------------------------------------------------------
 template <class T>
 static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double lmin, double lmax, int steps,
-                     const T* b, T* x, bool xzero) {
+                     const T* b, T* x, bool xzero, int kind) {
   size_t len = (size_t)M.rows * nr;
   double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta, rho = 1.0 / sigma;
   Tmp<T> d(c.pool, len), xt(c.pool, len);
@@ -82,12 +82,12 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
   if (xzero) {
     cheb_first<T>(c.ex, len, nr, dinv, b, 1.0 / theta, d, xa);
   } else {
-    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, 0.0, 1.0 / theta);
+    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, 0.0, 1.0 / theta, kind);
     std::swap(xa, xb);
   }
   for (int k = 1; k < steps; ++k) {
     double rn = 1.0 / (2.0 * sigma - rho);
-    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, rn * rho, 2.0 * rn / delta);
+    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, rn * rho, 2.0 * rn / delta, kind);
     std::swap(xa, xb);
     rho = rn;
   }
@@ -96,7 +96,8 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
 
 // M_Q^{-1} b by Chebyshev-Jacobi on the exact Wathen interval
 template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int steps) {
-  cheb_run<T>(c, c.MQ, 1, pick<T>(c.MQ_dinv64, c.MQ_dinv32), kMassLow, kMassHigh, std::max(1, steps), b, x, true);
+  cheb_run<T>(c, c.MQ, 1, pick<T>(c.MQ_dinv64, c.MQ_dinv32), kMassLow, kMassHigh, std::max(1, steps), b, x, true,
+              STOKES_KERNEL_SPMV_P1);
 }
 
 // ---------------------------------------------------------------------------
@@ -115,19 +116,20 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
   const T* dinv = which ? pick<T>(L.KQ_dinv64, L.KQ_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32);
   double lmax = kChebHigh * (which ? L.KQ_lmax : L.A3_lmax), lmin = kChebLow * (which ? L.KQ_lmax : L.A3_lmax);
   int deg = std::max(1, c.opt.cheb_degree);
-  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero);
+  const int kind = which ? STOKES_KERNEL_SPMV_P1 : (l == 0 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMM_A3_COARSE);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind);
   Level& Lc = c.lv[l + 1];
   const Csr& Mc = which ? Lc.KQ : Lc.A3;
   size_t lenc = (size_t)Mc.rows * nr;
   {
     Tmp<T> r(c.pool, len);
-    spmv_resid<T>(c.ex, M, nr, b, x, r, nr == 3 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMV_P1);
+    spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
     Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);
     spmv_store<T>(c.ex, which ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER);
     vcycle<T>(c, which, l + 1, bc, xc, true);
     spmv_add<T>(c.ex, which ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER);
   }
-  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind);
 }
 
 template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
@@ -522,7 +524,7 @@ static void correction(stokes_ctx& c, const double* rF, const double* rg, double
 static double full_residual(stokes_ctx& c, const double* F, const double* g, const double* U, const double* P,
                             double* rF, double* rg, double normFg) {
   const size_t nv = nvel(c), np = npres(c);
-  bsr3_apply<double>(c.ex, c.A, U, rF, F);
+  bsr3_apply<double>(c.ex, c.A, U, rF, F, STOKES_KERNEL_RESIDUAL);
   bt_apply<double>(c.ex, c.Bt, P, rF, (const double*)nullptr, rF, 1.0);
   b_apply<double>(c.ex, c.B, U, rg, g, -1.0);
   const int s = c.sc.take(2);

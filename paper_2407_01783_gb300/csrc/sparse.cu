@@ -464,8 +464,7 @@ template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T
   else launch(ex, m, SH_CSR1, x, EpiResid<T, 1>{b, y, (size_t)m.rows}, m.group);
 }
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin, T* d, T* xout,
-                                  const T* dinv, double c1, double c2) {
-  int kind = nr == 3 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMV_P1;
+                                  const T* dinv, double c1, double c2, int kind) {
   if (use_stencil<T>(m)) {
     ProfScope ps(ex, kind, stencil_bytes(*m.st, sizeof(T), nr, 4) + (double)sizeof(T) * m.rows);
     if (nr == 3) launch_stencil(ex, *m.st, 3, xin, EpiCheb<T, 3>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
@@ -477,8 +476,8 @@ template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T*
   if (nr == 3) launch(ex, m, SH_CSR3, xin, EpiCheb<T, 3>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
   else launch(ex, m, SH_CSR1, xin, EpiCheb<T, 1>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
 }
-template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b) {
-  ProfScope ps(ex, STOKES_KERNEL_SPMV_A, prod_bytes(m, sizeof(T), 3, 3, b ? 1 : 0));
+template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, int kind) {
+  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), 3, 3, b ? 1 : 0));
   if (b) launch(ex, m, SH_BSR3, x, EpiResid<T, 3>{b, y, (size_t)m.rows}, m.group);
   else launch(ex, m, SH_BSR3, x, EpiStore<T, 3>{y, (size_t)m.rows}, m.group);
 }
@@ -647,8 +646,8 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int);                            \
   template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int);                \
   template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
-                             double);                                                                     \
-  template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*);                          \
+                             double, int);                                                                     \
+  template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, int);                          \
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double);                     \
   template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double);          \
   template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*);

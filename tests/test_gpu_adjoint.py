@@ -1,0 +1,100 @@
+"""GPU checks of the adjoint solve and its autograd wrapper.
+
+J(u, p) = c . u + d . p (c at all P2 nodes, d at P1 nodes). The oracle's
+adjoint comes from the transposed bordered system: with K_b the bordered
+matrix of oracle.solve (its solution already has int p_h = 0),
+J = [c_U; d; 0]^T K_b^{-1} [F; g; 0], so dJ/d[F; g] = K_b^{-T} [c_U; d; 0],
+dJ/df = (rows of M_V)^T dJ/dF, dJ/dmu = -lambda_U^T E_V U. Finite differences:
+J is linear in f, so the central difference with unit step is exact up to the
+solver tolerance; in mu it is checked with a small relative step.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workload as wl
+from oracle.assemble import StokesSystem
+from oracle.mesh import KuhnMesh
+from oracle.solve import bordered_matrix, oracle_solve
+
+from gpu_helpers import cuda, gpu_module, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+N, MU, DT = 4, 0.3, 0.05
+
+
+def setup_case(seed=31):
+    sk = gpu_module()
+    V = wl.kuhn_vertices(N, 0.2, seed)
+    f = wl.random_force(N, seed + 1)
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal(((2 * N + 1) ** 3, 3))
+    d = rng.standard_normal((N + 1) ** 3)
+    return sk, V, f, c, d
+
+
+def J(sk, S, f, c, d, tol=1e-13):
+    u, p, _ = S.solve(cuda(f), None, tol)
+    return float((host(u) * c).sum() + host(p) @ d), host(u), host(p)
+
+
+def test_adjoint_matches_oracle_adjoint():
+    sk, V, f, c, d = setup_case()
+    S = sk.Stokes(N, V, MU, DT)
+    J0, u, p = J(sk, S, f, c, d)
+    dJdf, dJdg, dmu, info = S.adjoint(cuda(c), cuda(d), 1e-13)
+    orc = StokesSystem(KuhnMesh(N, V), MU, DT)
+    Kb = bordered_matrix(orc)
+    rhs = np.concatenate([orc.restrict_velocity(c), d, [0.0]])
+    lam = spla.splu(Kb.T.tocsc()).solve(rhs)
+    nv, npr = orc.A.shape[0], orc.B.shape[0]
+    lamU, lamP = lam[:nv], lam[nv:nv + npr]
+    dJdf_or = (orc.M_rows_all.T @ lamU.reshape(-1, 3))
+    assert rel_err(host(dJdf), dJdf_or) < 1e-9
+    # dJ/dg is defined up to a constant (sum(g) = 0): compare mean-free parts
+    gpu_g = host(dJdg)
+    assert rel_err(gpu_g - gpu_g.mean(), lamP - lamP.mean()) < 1e-8
+    Uo, Po = oracle_solve(orc, orc.load(f))
+    dmu_or = -lamU @ (orc.E @ Uo)
+    assert abs(dmu - dmu_or) < 1e-8 * abs(dmu_or), (dmu, dmu_or)
+    S.close()
+
+
+def test_adjoint_finite_differences():
+    sk, V, f, c, d = setup_case(41)
+    S = sk.Stokes(N, V, MU, DT)
+    J(sk, S, f, c, d)                      # the adjoint refers to the last forward solve
+    dJdf, _, dmu, _ = S.adjoint(cuda(c), cuda(d), 1e-13)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        v = rng.standard_normal(f.shape)
+        jp, _, _ = J(sk, S, f + v, c, d)
+        jm, _, _ = J(sk, S, f - v, c, d)
+        fd = (jp - jm) / 2.0
+        an = float((host(dJdf) * v).sum())
+        assert abs(fd - an) < 1e-9 * max(abs(an), 1e-30), (fd, an)
+    S.close()
+    h = 1e-4 * MU
+    Sp = sk.Stokes(N, V, MU + h, DT)
+    Sm = sk.Stokes(N, V, MU - h, DT)
+    fd_mu = (J(sk, Sp, f, c, d)[0] - J(sk, Sm, f, c, d)[0]) / (2 * h)
+    assert abs(fd_mu - dmu) < 1e-6 * abs(dmu), (fd_mu, dmu)
+    Sp.close()
+    Sm.close()
+
+
+def test_autograd_function():
+    sk, V, f, c, d = setup_case(51)
+    torch = pytest.importorskip("torch")
+    S = sk.Stokes(N, V, MU, DT)
+    ft = torch.tensor(f, device="cuda", requires_grad=True)
+    mu_t = torch.tensor(MU, dtype=torch.float64, device="cuda", requires_grad=True)
+    u, p = sk.StokesSolve.apply(S, ft, mu_t, 1e-13)
+    loss = (u * cuda(c)).sum() + (p * cuda(d)).sum()
+    loss.backward()
+    dJdf, _, dmu, _ = S.adjoint(cuda(c), cuda(d), 1e-13)
+    assert rel_err(host(ft.grad), host(dJdf)) < 1e-10
+    assert abs(float(mu_t.grad) - dmu) < 1e-10 * abs(dmu)
+    S.close()
