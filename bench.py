@@ -192,6 +192,24 @@ def ncu_traffic(kernel_name):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank helpers (replicas only: the ranks exchange nothing but timings)
+# ---------------------------------------------------------------------------
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (x itself when not distributed)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, solves_per_step, dofs, ms_per_step):
+    """Whole-job throughput: every rank solves its own replica of the workload."""
+    return world * solves_per_step * dofs / (ms_per_step / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -282,11 +300,7 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         ck = clocks.stop() if clocks else None
-        ms = e0.elapsed_time(e1) / steps
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
         return ms, infos, ck
 
     t_setup = time.perf_counter()
@@ -297,7 +311,7 @@ def run_ours(args):
     ms, infos, ck = timed(solvers, fs, outs, args.steps, args.warmup, clocks)
     worst = max(i["rel_residual"] for i in infos)
     bad = [i for i in infos if i["status"] != 0]
-    value = world * len(mus) * dofs / (ms / 1e3)
+    value = job_value(world, len(mus), dofs, ms)
 
     # per-kernel statistics: launches of every class and CUDA-event times of the
     # dominant class over the timed region; shares from the warm-up steps
@@ -334,11 +348,7 @@ def run_ours(args):
         barrier()
         if it >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_step = statistics.mean(e2e_ms) if e2e_ms else float("nan")
-    if dist is not None:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms) if e2e_ms else float("nan"), dist, dev)
     h2d = sum(a.nbytes for a in fh_np)
     d2h = sum(a.nbytes for a in uh) + sum(a.nbytes for a in ph)
     for S in solvers:
@@ -349,7 +359,7 @@ def run_ours(args):
     if prec == sk.PRECISION_MIXED and not args.no_fp64:
         s2, f2, o2 = make(sk.PRECISION_FP64, 0)
         ms64, inf64, _ = timed(s2, f2, o2, max(1, args.steps // 2), max(1, args.warmup // 2))
-        fp64 = {"value": world * len(mus) * dofs / (ms64 / 1e3), "ms_per_step": ms64,
+        fp64 = {"value": job_value(world, len(mus), dofs, ms64), "ms_per_step": ms64,
                 "worst_residual": max(i["rel_residual"] for i in inf64),
                 "iters": [(i["outer_iters"], i["inner_iters"], i["refinements"]) for i in inf64[:3]]}
         for S in s2:
@@ -359,7 +369,7 @@ def run_ours(args):
     if not args.no_coupled:
         s3, f3, o3 = make(prec, 0, method=sk.METHOD_COUPLED, block_lu=1)
         ms2, inf2, _ = timed(s3, f3, o3, max(1, args.steps // 2), max(1, args.warmup // 2))
-        coupled = {"value": world * len(mus) * dofs / (ms2 / 1e3), "ms_per_step": ms2,
+        coupled = {"value": job_value(world, len(mus), dofs, ms2), "ms_per_step": ms2,
                    "method": "coupled FGMRES(30), block-LU preconditioner, V-cycles for A~^{-1}",
                    "worst_residual": max(i["rel_residual"] for i in inf2),
                    "iters": [(i["outer_iters"], i["refinements"]) for i in inf2[:len(mus)]]}
@@ -376,7 +386,7 @@ def run_ours(args):
         "data": "synthetic (seeded jittered Kuhn mesh, manufactured solution)",
         "config": config(n, args.precision) if not args.mus else dict(config(n, args.precision), mus=list(mus)),
         "clocks": ck,
-        "e2e": {"value": world * len(mus) * dofs / (e2e_step / 1e3), "unit": UNIT,
+        "e2e": {"value": job_value(world, len(mus), dofs, e2e_step), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": int(total_launches),
         "roofline": roofline,

@@ -938,15 +938,49 @@ void to_f32(const Exec& ex, const double* src, float* dst, size_t n) {
   SK_CHECK_LAUNCH();
 }
 
-// Coarse vertices sit at the fine vertices with the same logical position.
-void subsample_vertices(int n, const double* Xf, double* Xc) {
-  int nc = n / 2, nvf = n + 1, nvc = nc + 1;
+// Coarse-level geometry: coarse vertex i sits at logical position i/nc; its
+// coordinates are the P1 interpolation of the fine (jittered) vertex
+// positions at that logical point on the fine Kuhn mesh. For nf = 2 nc this is
+// exactly the fine vertex 2i; for other ratios it is a smooth average of the
+// fine jitter, so coarse tetrahedra are no more distorted than fine ones.
+void subsample_vertices(int nf, int nc, const double* Xf, double* Xc) {
+  const int nvf = nf + 1, nvc = nc + 1;
   for (int k = 0; k <= nc; ++k)
     for (int j = 0; j <= nc; ++j)
       for (int i = 0; i <= nc; ++i) {
-        size_t fc = (size_t)(2 * i) + nvf * ((size_t)(2 * j) + (size_t)nvf * (2 * k));
-        size_t cc = (size_t)i + nvc * ((size_t)j + (size_t)nvc * k);
-        for (int c = 0; c < 3; ++c) Xc[3 * cc + c] = Xf[3 * fc + c];
+        const int ic[3] = {i, j, k};
+        int base[3];
+        double t[3];
+        for (int c = 0; c < 3; ++c) {
+          // y = ic * nf / nc in fine-cube units, exactly when the ratio is integral
+          long long num = (long long)ic[c] * nf;
+          int b = (int)(num / nc);
+          if (b > nf - 1) b = nf - 1;
+          base[c] = b;
+          t[c] = (double)(num - (long long)b * nc) / nc;
+        }
+        int p0 = 0, p1 = 1, p2 = 2;  // axes by decreasing local coordinate
+        if (t[p1] > t[p0]) std::swap(p0, p1);
+        if (t[p2] > t[p1]) std::swap(p1, p2);
+        if (t[p1] > t[p0]) std::swap(p0, p1);
+        const double lam[4] = {1.0 - t[p0], t[p0] - t[p1], t[p1] - t[p2], t[p2]};
+        int v[4][3];
+        for (int c = 0; c < 3; ++c) {
+          v[0][c] = base[c];
+          v[1][c] = base[c] + (c == p0);
+          v[2][c] = v[1][c] + (c == p1);
+          v[3][c] = base[c] + 1;
+        }
+        const size_t cc = (size_t)i + nvc * ((size_t)j + (size_t)nvc * k);
+        for (int c = 0; c < 3; ++c) {
+          double x = 0.0;
+          for (int l = 0; l < 4; ++l) {
+            if (lam[l] == 0.0) continue;
+            size_t fv = (size_t)v[l][0] + nvf * ((size_t)v[l][1] + (size_t)nvf * v[l][2]);
+            x += lam[l] * Xf[3 * fv + c];
+          }
+          Xc[3 * cc + c] = x;
+        }
       }
 }
 

@@ -115,17 +115,15 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   c.d_flag = c.arena.alloc<int>(1);
   SK_CUDA(cudaEventCreateWithFlags(&c.ev_read, cudaEventDisableTiming));
 
-  // level sizes n -> n/2 -> ... (nested Kuhn meshes)
+  // level sizes n -> ceil(n/2) -> ... down to at most 3 cubes per side (nested
+  // Kuhn meshes when n is even, logical-coordinate transfers otherwise)
   std::vector<int> ns{n};
-  while (ns.back() % 2 == 0 && ns.back() >= 4) ns.push_back(ns.back() / 2);
-  int nc = ns.back();
-  SK_REQUIRE((long long)(2 * nc - 1) * (2 * nc - 1) * (2 * nc - 1) <= 4096, STOKES_ERR_ARG,
-             "mesh size not supported: n must halve down to a coarsest level of at most 8 cubes per side");
+  while (ns.back() >= 4) ns.push_back((ns.back() + 1) / 2);
   std::vector<std::vector<double>> Xs(ns.size());
   Xs[0].assign(Xh, Xh + 3 * (size_t)(n + 1) * (n + 1) * (n + 1));
   for (size_t l = 1; l < ns.size(); ++l) {
     Xs[l].resize(3 * (size_t)(ns[l] + 1) * (ns[l] + 1) * (ns[l] + 1));
-    subsample_vertices(ns[l - 1], Xs[l - 1].data(), Xs[l].data());
+    subsample_vertices(ns[l - 1], ns[l], Xs[l - 1].data(), Xs[l].data());
   }
   for (double x : Xs[0]) SK_REQUIRE(std::isfinite(x), STOKES_ERR_ARG, "non-finite vertex coordinate");
 

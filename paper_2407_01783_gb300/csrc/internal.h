@@ -265,7 +265,7 @@ void diag_inverse(const Exec& ex, const Csr& m, double* dinv);
 // level size n, values copied from the assembled CSR m (FP64; FP32 on request).
 StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int p2, int n, const Csr& m);
 void to_f32(const Exec& ex, const double* src, float* dst, size_t n);
-void subsample_vertices(int n, const double* Xf_host, double* Xc_host);
+void subsample_vertices(int nf, int nc, const double* Xf_host, double* Xc_host);
 
 // ---------------------------------------------------------------------------
 // sparse products (sparse.cu); T = vector/matrix precision

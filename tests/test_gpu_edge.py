@@ -1,0 +1,103 @@
+"""Edge cases of the GPU path: smallest and odd meshes, degenerate right-hand
+sides, a one-level hierarchy, and the largest configuration."""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workload as wl
+from oracle.assemble import StokesSystem
+from oracle.mesh import KuhnMesh
+from oracle.solve import oracle_solve
+
+from gpu_helpers import aos, cuda, gpu_module, host, rel_err, soa
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 7])
+def test_small_and_odd_meshes_match_oracle(n):
+    """n = 2 is the smallest mesh (27 interior P2 nodes); odd n cannot be halved,
+    so the hierarchy has a single level solved by the dense coarse inverse."""
+    sk = gpu_module()
+    V = wl.kuhn_vertices(n, 0.2, 60 + n)
+    f = wl.random_force(n, 70 + n)
+    g = wl.random_pressure_load(n, 80 + n)
+    orc = StokesSystem(KuhnMesh(n, V), 0.05, 0.02)
+    Uo, Po = oracle_solve(orc, orc.load(f), g)
+    S = sk.Stokes(n, V, 0.05, 0.02)
+    u, p, info = S.solve(cuda(f), cuda(g), 1e-12)
+    assert rel_err(orc.restrict_velocity(host(u)), Uo) < 1e-9
+    assert rel_err(host(p), Po) < 1e-9
+    S.close()
+
+
+@pytest.mark.parametrize("n", [9, 11])
+def test_non_nested_hierarchies_match_oracle(n):
+    """Odd n coarsens to ceil(n/2) with logical-coordinate transfers (non-nested
+    spaces, interpolated coarse geometry); the solution is unaffected."""
+    sk = gpu_module()
+    V = wl.kuhn_vertices(n, 0.2, 90 + n)
+    f = wl.random_force(n, 91 + n)
+    orc = StokesSystem(KuhnMesh(n, V), 0.02, 0.01)
+    Uo, Po = oracle_solve(orc, orc.load(f))
+    S = sk.Stokes(n, V, 0.02, 0.01, options=sk.stokes_default_options(vcycles=1))
+    assert S.sizes["levels"] >= 3
+    u, p, info = S.solve(cuda(f), None, 1e-12)
+    assert rel_err(orc.restrict_velocity(host(u)), Uo) < 1e-9
+    assert rel_err(host(p), Po) < 1e-9
+    S.close()
+
+
+def test_non_nested_vcycle_contracts():
+    from test_gpu_multigrid import vcycle_stats
+    sk = gpu_module()
+    for n in (13, 15):
+        sym, rate = vcycle_stats(sk, n, 1e-2, 1e-3, "A3")
+        assert sym < 1e-10 and rate < 0.6, (n, rate)
+        sym, rate = vcycle_stats(sk, n, 1e-2, 1e-3, "KQ")
+        assert sym < 1e-10 and rate < 0.6, (n, rate)
+
+
+def test_zero_rhs_and_loose_tolerance():
+    sk = gpu_module()
+    n = 4
+    V = wl.kuhn_vertices(n, 0.2, 3)
+    S = sk.Stokes(n, V, 0.1, 0.01)
+    z = np.zeros(((2 * n + 1) ** 3, 3))
+    u, p, info = S.solve(cuda(z), None, 1e-10)
+    assert info.status == 0 and info.outer_iters == 0
+    assert np.abs(host(u)).max() == 0 and np.abs(host(p)).max() == 0
+    f = wl.random_force(n, 4)
+    u, p, info = S.solve(cuda(f), None, 1.0)                   # tol >= 1: nothing to do
+    assert info.status == 0 and info.outer_iters == 0 and np.abs(host(u)).max() == 0
+    S.close()
+
+
+def test_one_level_vcycle_is_exact_inverse():
+    """With a single level the V-cycle is the dense coarse inverse of A~_3."""
+    sk = gpu_module()
+    n = 2
+    V = wl.kuhn_vertices(n, 0.2, 8)
+    S = sk.Stokes(n, V, 0.3, 0.02, options=sk.stokes_default_options(vcycles=1))
+    orc = StokesSystem(KuhnMesh(n, V), 0.3, 0.02)
+    r = np.random.default_rng(1).standard_normal(3 * orc.n_inner)
+    z = aos(host(S.apply("VCYCLE_A3", cuda(soa(r)), r.size)))
+    ref = spla.spsolve(orc.A3s.tocsc(), r.reshape(-1, 3))
+    assert rel_err(z, ref.ravel()) < 1e-12
+    S.close()
+
+
+def test_largest_configuration_coupled_96():
+    """96^3 jittered mesh (22.5 M DOFs), Method 2, mixed precision: the largest
+    configuration solves to 1e-8."""
+    sk = gpu_module()
+    n, mu, dt = 96, 1e-3, 1e-3
+    V = wl.kuhn_vertices(n, 0.2, 3)
+    f = wl.manufactured_force(n, V, mu, dt, 3)
+    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1, method=1))
+    assert S.sizes["dofs"] == 21567171 + 912673
+    u, p, info = S.solve(cuda(f), None, 1e-8)
+    assert info.status == 0 and info.rel_residual <= 1e-8, info.as_dict()
+    assert np.isfinite(host(p)).all()
+    S.close()

@@ -1,0 +1,72 @@
+"""Parity at the benchmark's full size and in its launch configuration.
+
+The 48^3 jittered workload (seed 2, dt = 1e-3, mixed precision, one V-cycle)
+is solved on the GPU to a true relative residual of 1e-8. The oracle cannot
+solve it, but it evaluates residual rows at sampled nodes from the incident
+elements (oracle.local, pinned against the global assembly). Because
+|r_i| <= ||r||_2 <= tol ||[F; g]||_2 holds for every row, each sampled row is
+checked against that bound, and the sampled rows' root mean square (scaled to
+the full row count) is checked against the tolerance as well.
+"""
+
+import numpy as np
+import pytest
+
+import workload as wl
+from oracle.local import load_norm, pressure_residual_rows, velocity_residual_rows
+from oracle.mesh import KuhnMesh
+
+from gpu_helpers import cuda, gpu_module, host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+def sampled_check(n, V, mu, dt, f, u, p, mesh, seed=0, kv=160, kp=80):
+    rng = np.random.default_rng(seed)
+    vel_nodes = rng.choice(mesh.interior, kv, replace=False)
+    vel_nodes[:8] = mesh.interior[:8]              # include nodes next to the boundary
+    p_nodes = rng.choice(mesh.n_p1, kp, replace=False)
+    rv = velocity_residual_rows(mesh, mu, dt, f, u, p, vel_nodes)
+    rp = pressure_residual_rows(mesh, u, None, p_nodes)
+    normF = load_norm(mesh, f)
+    bound = TOL * normF
+    assert np.abs(rv).max() <= bound and np.abs(rp).max() <= bound, (np.abs(rv).max(), np.abs(rp).max(), bound)
+    nrows = 3 * mesh.interior.size + mesh.n_p1
+    est = np.sqrt((np.sum(rv ** 2) + np.sum(rp ** 2)) / (rv.size + rp.size) * nrows) / normF
+    return est
+
+
+@pytest.fixture(scope="module")
+def workload48():
+    n, mu_list, dt = 48, (1.0, 1e-2, 1e-4), 1e-3
+    V = wl.kuhn_vertices(n, 0.2, 2)
+    return n, V, mu_list, dt, KuhnMesh(n, V)
+
+
+@pytest.mark.parametrize("imu", [0, 1, 2])
+def test_bench_workload_method1_mixed(workload48, imu):
+    sk = gpu_module()
+    n, V, mus, dt, mesh = workload48
+    mu = mus[imu]
+    f = wl.manufactured_force(n, V, mu, dt, 2)
+    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1))
+    u, p, info = S.solve(cuda(f), None, TOL)
+    assert info.status == 0 and info.rel_residual <= TOL
+    est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=imu)
+    assert est <= 2 * TOL, est
+    S.close()
+
+
+def test_bench_workload_method2_mixed(workload48):
+    sk = gpu_module()
+    n, V, mus, dt, mesh = workload48
+    mu = 1e-2
+    f = wl.manufactured_force(n, V, mu, dt, 2)
+    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1, method=1))
+    u, p, info = S.solve(cuda(f), None, TOL)
+    assert info.status == 0 and info.rel_residual <= TOL
+    est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=7)
+    assert est <= 2 * TOL, est
+    S.close()
