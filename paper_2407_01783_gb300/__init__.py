@@ -23,7 +23,7 @@ from ._lib import (KERNEL, MAT, METHOD_COUPLED, METHOD_SCHUR, OP, PRECISION_FP64
                    PRECISION_MIXED, SCHUR_PREC_LAPLACE, SCHUR_PREC_LUMPED, StokesInfo,
                    StokesOptions)
 
-__all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "stokes_default_options",
+__all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "StokesBatch", "stokes_default_options",
            "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_adjoint",
            "stokes_destroy", "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_export", "stokes_sizes",
            "stokes_kernel_stats", "stokes_kernel_stats_reset", "stokes_profile_mode", "StokesSolve", "OP", "MAT",
@@ -174,12 +174,14 @@ class Stokes:
     """Owning wrapper: one mesh, one (mu, dt, gamma), reusable across solves."""
 
     def __init__(self, n: int, vertices, mu: float, dt: float, gamma: float = 0.0,
-                 options: StokesOptions | None = None, device: str | torch.device = "cuda"):
+                 options: StokesOptions | None = None, device: str | torch.device = "cuda",
+                 stream: torch.cuda.Stream | None = None):
         self.n, self.mu, self.dt, self.gamma = n, mu, dt, gamma
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
             self.options = options if options is not None else stokes_default_options()
-            self.ctx = stokes_setup(n, vertices, mu, dt, gamma, self.options)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.ctx = stokes_setup(n, vertices, mu, dt, gamma, self.options, self.stream)
         self.sizes = stokes_sizes(self.ctx)
 
     def close(self):
@@ -242,6 +244,60 @@ class Stokes:
 
     def kernel_stats(self, kernel: str):
         return stokes_kernel_stats(self.ctx, KERNEL[kernel])
+
+
+class StokesBatch:
+    """Many independent instances of uneven size solved concurrently.
+
+    Each instance has its own context and CUDA stream; ``solve_all`` issues
+    every instance's right-hand sides from its own host thread (the C calls
+    release the GIL), so the kernels of all instances overlap on the GPU.
+    """
+
+    def __init__(self, instances, options: StokesOptions | None = None,
+                 device: str | torch.device = "cuda"):
+        self.device = torch.device(device)
+        self.solvers = []
+        for (n, vertices, mu, dt, gamma) in instances:
+            st = torch.cuda.Stream(self.device)
+            self.solvers.append(Stokes(n, vertices, mu, dt, gamma, options, self.device, st))
+
+    def close(self):
+        for S in self.solvers:
+            S.close()
+
+    @property
+    def dofs(self):
+        return [S.sizes["dofs"] for S in self.solvers]
+
+    def solve_all(self, forces, tol: float = 1e-8, outs=None):
+        """forces[i]: list of device tensors [(2n_i+1)^3, 3] for instance i.
+        Returns (outs, infos, device_ms): outs[i][k] = (u, p)."""
+        import concurrent.futures as cf
+        if outs is None:
+            outs = [[(torch.empty_like(f), torch.empty(S.n_p1, dtype=torch.float64, device=self.device))
+                     for f in fl] for S, fl in zip(self.solvers, forces)]
+        start = torch.cuda.Event(enable_timing=True)
+        ends = [torch.cuda.Event(enable_timing=True) for _ in self.solvers]
+        launch = torch.cuda.current_stream(self.device)
+        start.record(launch)
+        for S in self.solvers:
+            S.stream.wait_event(start)
+        infos = [None] * len(self.solvers)
+
+        def run(i):
+            S = self.solvers[i]
+            res = []
+            for f, (u, p) in zip(forces[i], outs[i]):
+                res.append(stokes_solve(S.ctx, f, None, tol, u, p).as_dict())
+            ends[i].record(S.stream)
+            infos[i] = res
+
+        with cf.ThreadPoolExecutor(max_workers=len(self.solvers)) as ex:
+            list(ex.map(run, range(len(self.solvers))))
+        torch.cuda.synchronize(self.device)
+        ms = max(start.elapsed_time(e) for e in ends)
+        return outs, infos, ms
 
 
 class StokesSolve(torch.autograd.Function):

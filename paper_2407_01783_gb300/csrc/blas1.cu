@@ -152,17 +152,15 @@ __global__ void k_cg_update(size_t n, Coef a, const T* __restrict__ d, T* __rest
   SK_COEF2(a, a, ad, unused);
   (void)unused;
   SK_IDX;
-  if (i == 0 && a.den && !(*a.den > 0.0)) atomicOr(flag, 1);  // p^T A p <= 0: breakdown
+  if (i == 0 && flag && a.den && !(*a.den > 0.0)) atomicOr(flag, 1);  // p^T A p <= 0: breakdown
   const T av = (T)ad;
   x[i] += av * d[i];
   if (r) r[i] -= av * q[i];
 }
-static int* g_flag = nullptr;  // set by the context before solves
-void set_breakdown_flag(int* f) { g_flag = f; }
 template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r) {
   if (!n) return;
   ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * (r ? 6 : 3));
-  k_cg_update<T><<<SK_GRID(n)>>>(n, a, d, x, q, r, g_flag);
+  k_cg_update<T><<<SK_GRID(n)>>>(n, a, d, x, q, r, ex.flag);
   SK_CHECK_LAUNCH();
 }
 

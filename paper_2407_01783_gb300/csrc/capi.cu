@@ -113,6 +113,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   c.ds.counter = c.arena.alloc<unsigned>(1);
   SK_CUDA(cudaMemsetAsync(c.ds.counter, 0, sizeof(unsigned), c.ex.s));
   c.d_flag = c.arena.alloc<int>(1);
+  c.ex.flag = c.d_flag;
   SK_CUDA(cudaEventCreateWithFlags(&c.ev_read, cudaEventDisableTiming));
 
   // level sizes n -> ceil(n/2) -> ... down to at most 3 cubes per side (nested

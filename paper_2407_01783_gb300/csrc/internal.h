@@ -61,6 +61,7 @@ struct Prof {
 struct Exec {
   cudaStream_t s = nullptr;
   Prof* prof = nullptr;
+  int* flag = nullptr;  // per-context status bits set by kernels (1: CG breakdown)
 };
 
 // Brackets one launch with events when profiling is on.
@@ -377,7 +378,6 @@ int adjoint_context(stokes_ctx* c, const double* dJdu, const double* dJdp, doubl
                     double* dJdf, double* dJdg, double* dJdmu, stokes_info* info);
 void apply_operator(stokes_ctx* c, int op, int level, const double* x, double* y);
 double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps, uint64_t seed);
-void set_breakdown_flag(int* f);
 void set_last_error(const std::string& msg);  // message returned by stokes_last_error()
 void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
 }  // namespace sk

@@ -13,7 +13,6 @@
 
 namespace sk {
 
-void set_breakdown_flag(int* f);
 void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
 
 // Smoother interval [kChebLow, kChebHigh] x (Lanczos estimate of lambda_max(D^{-1}A)).
@@ -546,7 +545,6 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
   c.outer_iters = c.inner_iters = c.schur_inner_iters = 0;
   c.outer_capped = c.inner_capped = false;
   SK_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.ex.s));
-  set_breakdown_flag(c.d_flag);
   Tmp<double> gz(c.pool, np), rF(c.pool, nv), rg(c.pool, np);
   const double* gp = g;
   if (!gp) {
