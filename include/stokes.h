@@ -93,8 +93,9 @@ typedef struct {
                             correction pass (outer Krylov tolerance per pass);
                             its inner velocity solves get max(inner_tol,
                             pass_tol/30). Default 3e-2. */
-  int format;            /* 0: stencil-structured storage where the mesh allows
-                            (A~_3, eps M_Q + L_Q, M_Q, L_Q), 1: CSR everywhere */
+  int format;            /* 0: stencil-structured storage for A~_3, eps M_Q + L_Q,
+                            M_Q, L_Q on levels with >= 2^18 rows, CSR below;
+                            1: CSR everywhere; 2: stencil storage on every level */
 } stokes_options;
 
 typedef struct {

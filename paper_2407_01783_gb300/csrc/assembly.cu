@@ -836,7 +836,7 @@ void diag_inverse(const Exec& ex, const Csr& m, double* dinv) {
 // ---------------------------------------------------------------------------
 // stencil-structured storage (see StencilOp in internal.h)
 // ---------------------------------------------------------------------------
-StArgs stencil_args(const StencilOp& so, int block) {
+StArgs stencil_args(const StencilOp& so, int block, int rows_per_thread) {
   StArgs a;
   std::memset(&a, 0, sizeof(a));
   a.p2 = so.p2;
@@ -845,15 +845,18 @@ StArgs stencil_args(const StencilOp& so, int block) {
   a.lo = so.p2 ? 1 : 0;
   a.hi = so.p2 ? 2 * so.n - 1 : 2 * so.n;
   a.m = so.p2 ? 2 * so.n - 1 : so.n + 1;
+  a.R = rows_per_thread;
   int b = 0;
   for (int c = 0; c < so.ncls; ++c) {
     a.rows[c] = so.rows[c];
     a.S[c] = so.S[c];
     a.dbeg[c] = so.dbeg[c];
     a.voff[c] = so.voff[c];
+    a.pext[c] = so.pext[c];
+    a.prows[c] = so.prows[c];
     for (int k = 0; k < 3; ++k) a.ext[c][k] = so.ext[c][k], a.q0[c][k] = so.q0[c][k];
     a.bbeg[c] = b;
-    b += cdiv(so.rows[c], block);
+    b += cdiv(so.prows[c] / rows_per_thread, block);
   }
   a.bbeg[so.ncls] = b;
   for (int e = 0; e < so.nd; ++e) {
@@ -863,23 +866,24 @@ StArgs stencil_args(const StencilOp& so, int block) {
   return a;
 }
 
+// one thread per padded row: values of entry e at voff[c] + e * prows[c] + pr
 __global__ void k_stencil_fill(const StArgs a, const int* __restrict__ rp, const int* __restrict__ col,
                                const double* __restrict__ val, double* __restrict__ out) {
-  int c, r;
-  if (!st_locate(a, c, r)) return;
-  int qx, qy, qz;
-  st_coords(a, c, r, qx, qy, qz);
-  const int row = st_index(a, qx, qy, qz);
-  const int lo = rp[row], hi = rp[row + 1];
+  int c, pr;
+  if (!st_locate(a, c, pr)) return;
+  int i, qx, qy, qz;
+  st_coords(a, c, pr, i, qx, qy, qz);
+  const bool real = i < a.ext[c][0];
+  const int row = real ? st_index(a, qx, qy, qz) : 0;
+  const int lo = real ? rp[row] : 0, hi = real ? rp[row + 1] : 0;
   for (int e = 0; e < a.S[c]; ++e) {
     const int de = a.dbeg[c] + e;
-    const int nx = qx + a.d[de][0], ny = qy + a.d[de][1], nz = qz + a.d[de][2];
     double w = 0.0;
-    if (st_inside(a, nx, ny, nz)) {
+    if (real && st_inside(a, qx + a.d[de][0], qy + a.d[de][1], qz + a.d[de][2])) {
       int pos = find_col(col, lo, hi, row + a.lin[de]);
       if (pos >= 0) w = val[pos];
     }
-    out[a.voff[c] + (size_t)e * a.rows[c] + r] = w;
+    out[a.voff[c] + (size_t)e * a.prows[c] + pr] = w;
   }
 }
 
@@ -900,6 +904,8 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
       so->ext[c][k] = p2 ? (par ? n : n - 1) : n + 1;
     }
     so->rows[c] = so->ext[c][0] * so->ext[c][1] * so->ext[c][2];
+    so->pext[c] = (so->ext[c][0] + kStencilRows - 1) / kStencilRows * kStencilRows;
+    so->prows[c] = so->pext[c] * so->ext[c][1] * so->ext[c][2];
     so->dbeg[c] = nd;
     for (int e = st->beg[kind][c]; e < st->beg[kind][c + 1]; ++e) {
       SK_REQUIRE(nd < kMaxStencil, STOKES_ERR_ARG, "stencil table overflow");
@@ -912,7 +918,7 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
     }
     so->S[c] = nd - so->dbeg[c];
     so->voff[c] = off;
-    off += (long long)so->S[c] * so->rows[c];
+    off += (long long)so->S[c] * so->prows[c];
   }
   so->nd = nd;
   so->total = off;
@@ -921,7 +927,7 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
   SK_REQUIRE(off < (1LL << 32) && 3 * rows_all < (1LL << 32), STOKES_ERR_ARG,
              "stencil storage needs 32-bit indices (mesh too large)");
   so->v64 = ar.alloc<double>(off);
-  StArgs a = stencil_args(*so, 128);
+  StArgs a = stencil_args(*so, 128, 1);
   k_stencil_fill<<<a.bbeg[so->ncls], 128, 0, ex.s>>>(a, m.rowptr, m.col, m.v64, so->v64);
   SK_CHECK_LAUNCH();
   return so;

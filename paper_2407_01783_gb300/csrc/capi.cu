@@ -188,9 +188,9 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     build_transfer_p2(c.ex, c.arena, c.lv[l].n, c.lv[l + 1].n, c.lv[l].P2, c.lv[l].R2);
     build_transfer_p1(c.ex, c.arena, c.lv[l].n, c.lv[l + 1].n, c.lv[l].P1, c.lv[l].R1);
   }
-  if (c.opt.format == 0) {
+  if (c.opt.format != 1) {
     auto add = [&](Csr& m, int p2, int nn) {
-      if (m.rows < kStencilMinRows) return;
+      if (c.opt.format == 0 && m.rows < kStencilMinRows) return;
       c.stencils.emplace_back(stencil_from_csr(c.ex, c.arena, st, p2, nn, m));
       m.st = c.stencils.back().get();
     };
@@ -362,7 +362,7 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
   if (!c) return STOKES_ERR_OOM;
   if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
   if (c->opt.vcycles < 1 || c->opt.cheb_degree < 1 || c->opt.restart < 2 || !(c->opt.eps_pressure > 0) ||
-      !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 1 ||
+      !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 2 ||
       !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1)) {
     g_last_error = "stokes_setup: invalid options";
     delete c;

@@ -83,11 +83,16 @@ struct ProfScope {
 // same-class rows reads 128 contiguous bytes per entry.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStencil = 256;
+// Rows of one class along x are grouped by kStencilRows per thread; the value
+// layout pads each class's x-extent to a multiple of kStencilRows so that the
+// values of a thread's rows are one aligned vector.
+constexpr int kStencilRows = 1;
 struct StencilOp {
   int p2 = 1;                // 1: interior P2 index space, 0: P1 index space
   int n = 0;
   int ncls = 0;
   int rows[8] = {}, ext[8][3] = {}, q0[8][3] = {}, S[8] = {}, dbeg[8] = {};
+  int pext[8] = {}, prows[8] = {};  // padded x-extent and padded row count per class
   long long voff[8] = {};
   long long total = 0;       // stored entries (all classes)
   signed char d[kMaxStencil][3] = {};  // half-grid offsets of entry e
@@ -103,29 +108,33 @@ template <> inline float* StencilOp::v<float>() const { return v32; }
 // Kernel-side view of a StencilOp (passed by value; blocks of one class are
 // contiguous: class c owns blocks [bbeg[c], bbeg[c+1])).
 struct StArgs {
-  int p2, n, ncls, lo, hi, m;
-  int rows[8], ext[8][3], q0[8][3], S[8], dbeg[8];
+  int p2, n, ncls, lo, hi, m, R;  // R: rows per thread of the launch using these args
+  int rows[8], ext[8][3], q0[8][3], S[8], dbeg[8], pext[8], prows[8];
   long long voff[8];
   int bbeg[9];
   signed char d[kMaxStencil][3];
   int lin[kMaxStencil];
 };
-StArgs stencil_args(const StencilOp& s, int block);
+StArgs stencil_args(const StencilOp& s, int block, int rows_per_thread);
 
 #ifdef __CUDACC__
 // class and row-in-class of this thread; false if past the class end
-__device__ __forceinline__ bool st_locate(const StArgs& a, int& c, int& r) {
+// class c and thread-in-class t; each thread owns a.R consecutive padded
+// rows of one x-line: padded row index pr = t * a.R
+__device__ __forceinline__ bool st_locate(const StArgs& a, int& c, int& t) {
   c = 0;
 #pragma unroll 1
   while (c + 1 < a.ncls && (int)blockIdx.x >= a.bbeg[c + 1]) ++c;
-  r = ((int)blockIdx.x - a.bbeg[c]) * (int)blockDim.x + (int)threadIdx.x;
-  return r < a.rows[c];
+  t = ((int)blockIdx.x - a.bbeg[c]) * (int)blockDim.x + (int)threadIdx.x;
+  return t * a.R < a.prows[c];
 }
-__device__ __forceinline__ void st_coords(const StArgs& a, int c, int r, int& qx, int& qy, int& qz) {
-  const int ex = a.ext[c][0], ey = a.ext[c][1];
-  qx = a.q0[c][0] + 2 * (r % ex);
-  qy = a.q0[c][1] + 2 * ((r / ex) % ey);
-  qz = a.q0[c][2] + 2 * (r / (ex * ey));
+// padded row pr -> x index i (may be >= ext: padding) and coordinates
+__device__ __forceinline__ void st_coords(const StArgs& a, int c, int pr, int& i, int& qx, int& qy, int& qz) {
+  const int px = a.pext[c], ey = a.ext[c][1];
+  i = pr % px;
+  qx = a.q0[c][0] + 2 * i;
+  qy = a.q0[c][1] + 2 * ((pr / px) % ey);
+  qz = a.q0[c][2] + 2 * (pr / (px * ey));
 }
 // index of half-grid node q in the matrix's index space
 __device__ __forceinline__ int st_index(const StArgs& a, int qx, int qy, int qz) {

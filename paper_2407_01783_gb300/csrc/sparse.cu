@@ -310,24 +310,30 @@ __global__ void __launch_bounds__(256) k_bt(int rows, const int* __restrict__ rp
 }
 
 // Stencil-structured product (StencilOp): one thread per row; a block holds
-// rows of one class, so the entry loop, the offsets and the strides are
-// uniform across the warp. Interior rows (all neighbours inside the index
-// space) skip the bounds test.
+// rows of one class, so the entry loop, offsets and strides are uniform
+// across the warp and consecutive lanes gather from nodes 2 apart.
+// Fast path: if every y neighbour is inside the index space and every z
+// neighbour is strictly inside (not on the first or last z plane), then for any
+// x offset in [-2, 2] the neighbour index row + lin[e] lies in [0, size): the
+// smallest reachable index is >= m - 2 and the largest <= m^3 - m^2 + 1 (m the
+// points per axis). An x-neighbour outside the space may wrap into the
+// adjacent line, but its stored weight is exactly 0. So rows need no test
+// except near the y/z boundary, and no warp diverges at x-line ends.
 template <int NR, class TM, class T, class Epi>
-__global__ void __launch_bounds__(256) k_stencil(const StArgs a, const TM* __restrict__ v, const T* __restrict__ x,
+__global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __restrict__ v, const T* __restrict__ x,
                                                  size_t xs, Epi epi) {
   int c, r;
   if (!st_locate(a, c, r)) return;
-  int qx, qy, qz;
-  st_coords(a, c, r, qx, qy, qz);
+  int i, qx, qy, qz;
+  st_coords(a, c, r, i, qx, qy, qz);
+  if (i >= a.ext[c][0]) return;  // padding row
   const int row = st_index(a, qx, qy, qz);
-  const bool inner = qx - 2 >= a.lo && qx + 2 <= a.hi && qy - 2 >= a.lo && qy + 2 <= a.hi && qz - 2 >= a.lo &&
-                     qz + 2 <= a.hi;
+  const bool inner = qy - 2 >= a.lo && qy + 2 <= a.hi && qz - 2 > a.lo && qz + 2 < a.hi;
   T acc[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc[q] = T(0);
   const TM* vr = v + a.voff[c] + r;
-  const size_t rc = (size_t)a.rows[c];
+  const size_t rc = (size_t)a.prows[c];
   const int S = a.S[c], db = a.dbeg[c];
   if (inner) {
 #pragma unroll 4
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(256) k_stencil(const StArgs a, const TM* __res
 template <class T, class Epi>
 static void launch_stencil(const Exec& ex, const StencilOp& so, int nr, const T* x, const Epi& epi) {
   const int bs = 128;
-  StArgs a = stencil_args(so, bs);
+  StArgs a = stencil_args(so, bs, kStencilRows);
   int grid = a.bbeg[so.ncls];
   if (grid == 0) return;
   size_t xs = 0;

@@ -106,6 +106,26 @@ def test_operator_products(pair):
     assert rel_err(aos(host(S.apply("LOAD", cuda(f), nv))), orc.load(f)) < 1e-13
 
 
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_operator_products_every_storage(fmt):
+    """The same products with CSR everywhere (1) and stencil storage on every
+    level (2): the stencil kernel's boundary and interior paths on small meshes."""
+    sk = gpu_module()
+    for n in (3, 4, 6, 9):
+        V = wl.kuhn_vertices(n, 0.2, 40 + n)
+        S = sk.Stokes(n, V, 0.2, 0.03, options=sk.stokes_default_options(format=fmt))
+        orc = StokesSystem(KuhnMesh(n, V), 0.2, 0.03)
+        rng = np.random.default_rng(n)
+        x = rng.standard_normal(orc.A.shape[0])
+        p = rng.standard_normal(orc.B.shape[0])
+        nv, np_ = x.size, p.size
+        assert rel_err(aos(host(S.apply("A3", cuda(soa(x)), nv))), (orc.A3s @ x.reshape(-1, 3)).ravel()) < 1e-13
+        assert rel_err(host(S.apply("KQ", cuda(p), np_)), (orc.MQ + orc.LQ) @ p) < 1e-13
+        assert rel_err(host(S.apply("MQ", cuda(p), np_)), orc.MQ @ p) < 1e-13
+        assert rel_err(host(S.apply("LQ", cuda(p), np_)), orc.LQ @ p) < 1e-13
+        S.close()
+
+
 def test_augmented_operator_matches_definition():
     """A_gamma x = A x + gamma mu B^T M_Q^{-1} B x (Eq. def_of_Alambda); M_Q^{-1} by
     Chebyshev (24 steps on [1/2, 5/2], error below 0.382^24 ~ 1e-10)."""

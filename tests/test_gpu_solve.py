@@ -53,6 +53,11 @@ def test_config1_laplacian_preconditioner():
     assert r["eu"] <= PARITY and r["ep"] <= PARITY, r
 
 
+def test_config1_stencil_storage_everywhere():
+    r = run_case(8, 1e-2, 1e-2, 0.0, 1, format=2)
+    assert r["eu"] <= PARITY and r["ep"] <= PARITY, r
+
+
 @pytest.mark.parametrize("mu", [1.0, 1e-2, 1e-4])
 def test_jittered_with_pressure_load(mu):
     r = run_case(6, mu, 1e-3, 0.2, 3, g_seed=4)
@@ -81,9 +86,9 @@ def test_method2_inner_cg_with_gamma():
     assert r["eu"] <= PARITY and r["ep"] <= PARITY, r
 
 
-@pytest.mark.parametrize("method", [0, 1])
-def test_mixed_precision_reaches_1e8(method):
-    r = run_case(8, 1e-2, 1e-3, 0.2, 2, tol=1e-8, precision=1, method=method)
+@pytest.mark.parametrize("method,fmt", [(0, 0), (1, 0), (0, 2), (1, 2)])
+def test_mixed_precision_reaches_1e8(method, fmt):
+    r = run_case(8, 1e-2, 1e-3, 0.2, 2, tol=1e-8, precision=1, method=method, format=fmt)
     assert r["info"]["status"] == 0 and r["res"] <= 1.5e-8, r
     # error against the FP64 oracle, stated per result (no fixed bar beyond the residual)
     print("mixed", method, "eu", r["eu"], "ep", r["ep"], r["info"])
