@@ -244,7 +244,8 @@ def run_ours(args):
     def make(precision, profile, **extra):
         solvers, fs, outs = [], [], []
         for mu in mus:
-            opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles, **extra)
+            opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles,
+                                            schur_inner_iters=args.schur_inner_iters, **extra)
             S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
             f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
             u = torch.empty_like(f)
@@ -475,6 +476,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch line")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
+    ap.add_argument("--schur-inner-iters", type=int, default=2,
+                    help="fixed PCG iterations inside C (0: stop at the inner tolerance)")
     ap.add_argument("--cpu-baseline-worker", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_worker:

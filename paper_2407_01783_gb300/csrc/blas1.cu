@@ -11,7 +11,12 @@ namespace sk {
 
 __device__ __forceinline__ double coef_value(const Coef& k) {
   double v = k.c;
-  if (k.num) v += k.s * (*k.num) / (k.den ? *k.den : 1.0);
+  if (k.num) {
+    const double den = k.den ? *k.den : 1.0;
+    // a zero denominator only arises when the Krylov vectors vanished (exact
+    // convergence inside a fixed-iteration solve): contribute nothing
+    if (den != 0.0) v += k.s * (*k.num) / den;
+  }
   return v;
 }
 
@@ -95,14 +100,16 @@ __global__ void __launch_bounds__(256) k_dots(DotArgs<T> a) {
 }
 
 template <class T>
-void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const T* const* y, size_t n, double* out) {
+void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const T* const* y, size_t n, double* out,
+          int mode) {
   SK_REQUIRE(k >= 1 && k <= kMaxDots, STOKES_ERR_ARG, "dots: bad count");
   ProfScope ps(ex, STOKES_KERNEL_BLAS1, 0.0 + (double)sizeof(T) * n * (2.0 * k));
   DotArgs<T> a{};
   for (int j = 0; j < k; ++j) a.x[j] = x[j], a.y[j] = y ? y[j] : nullptr;
   a.k = k;
   a.n = n;
-  a.compensated = std::is_same<T, float>::value && n >= kCompensatedMin;
+  a.compensated = std::is_same<T, float>::value &&
+                  (mode == kDotFast || (mode == kDotAuto && n >= kCompensatedMin));
   a.partial = ds.partial;
   a.counter = ds.counter;
   a.out = out;
@@ -299,7 +306,7 @@ void scalar_sub(const Exec& ex, double* out, const double* a, const double* b) {
 
 #define SK_INST1(T)                                                                                     \
   template void dots<T>(const Exec&, const DotScratch&, int, const T* const*, const T* const*, size_t, \
-                        double*);                                                                       \
+                        double*, int);                                                                       \
   template void axpby<T>(const Exec&, size_t, Coef, const T*, Coef, T*);                               \
   template void cg_update<T>(const Exec&, size_t, Coef, const T*, T*, const T*, T*);                   \
   template void scale_copy<T>(const Exec&, size_t, Coef, const T*, T*);                                \

@@ -318,8 +318,12 @@ constexpr size_t kCompensatedMin = (size_t)1 << 20;
 // grids are latency-bound with one thread per row and stay CSR.
 constexpr int kStencilMinRows = 1 << 18;
 // out[i] = sum_j x_i[j] * y_i[j] for i < k (y_i == nullptr means all ones).
+// Accumulation of FP32 dot products: kDotAuto = compensated FP32 partial sums
+// for vectors of at least kCompensatedMin entries, kDotFast = compensated for
+// any length (inner solves), kDotExact = FP64 throughout (outer Krylov).
+enum { kDotAuto = 0, kDotFast = 1, kDotExact = 2 };
 template <class T> void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x,
-                             const T* const* y, size_t n, double* out);
+                             const T* const* y, size_t n, double* out, int mode = kDotAuto);
 template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y);
 // x += a d; r -= a q   (a from device scalars)
 template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r);

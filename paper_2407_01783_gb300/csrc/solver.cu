@@ -44,10 +44,11 @@ static double read_wait(stokes_ctx& c, int slot) {
   return c.sc.h[slot];
 }
 
-template <class T> static void dot1(stokes_ctx& c, const T* x, const T* y, size_t n, double* out) {
+template <class T>
+static void dot1(stokes_ctx& c, const T* x, const T* y, size_t n, double* out, int mode = kDotAuto) {
   const T* xs[1] = {x};
   const T* ys[1] = {y};
-  dots<T>(c.ex, c.ds, 1, xs, ys, n, out);
+  dots<T>(c.ex, c.ds, 1, xs, ys, n, out, mode);
 }
 template <class T> static void copy(stokes_ctx& c, T* dst, const T* src, size_t n) {
   SK_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, c.ex.s));
@@ -57,9 +58,9 @@ template <class T> static void zero(stokes_ctx& c, T* p, size_t n) {
 }
 // r <- r - mean(r) (Euclidean complement of the constants: pressure residuals
 // live there because B^T 1 = 0)
-template <class T> static void project_mean(stokes_ctx& c, T* r, size_t n) {
+template <class T> static void project_mean(stokes_ctx& c, T* r, size_t n, int mode = kDotExact) {
   int s = c.sc.take(1);
-  dot1<T>(c, r, (const T*)nullptr, n, c.sc.d + s);
+  dot1<T>(c, r, (const T*)nullptr, n, c.sc.d + s, mode);
   sub_mean<T>(c.ex, n, c.sc.d + s, (double)n, r);
   c.sc.give(1);
 }
@@ -140,45 +141,58 @@ template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* 
 // preconditioned CG. The residual norm of step k is copied to the host while
 // the preconditioner of step k+1 runs, so the GPU never idles on the check.
 // ---------------------------------------------------------------------------
+// fixed > 0: exactly `fixed` iterations and no host synchronisation at all.
 template <class T, class Op, class Pre>
 static int pcg(stokes_ctx& c, size_t n, Op&& op, Pre&& pre, const T* b, T* x, double rtol, int maxit,
-               bool* converged = nullptr) {
+               bool* converged = nullptr, int fixed = 0) {
   Scalars& S = c.sc;
   const int s = S.take(5);
   double* D = S.d + s;  // 0,1: r.z (alternating), 2: d.q, 3: r.r, 4: b.b
   Tmp<T> r(c.pool, n), z(c.pool, n), d(c.pool, n), q(c.pool, n);
   zero<T>(c, x, n);
   copy<T>(c, r, b, n);
-  dot1<T>(c, (const T*)r, (const T*)r, n, D + 4);
-  double bb = read_now(c, D + 4, s + 4);
-  if (!std::isfinite(bb)) throw Error(STOKES_ERR_NAN, "non-finite right-hand side in an inner solve");
+  double bn = 0.0;
   if (converged) *converged = true;
-  if (bb == 0.0) {
-    S.give(5);
-    return 0;
+  if (fixed <= 0) {
+    dot1<T>(c, (const T*)r, (const T*)r, n, D + 4, kDotFast);
+    double bb = read_now(c, D + 4, s + 4);
+    if (!std::isfinite(bb)) throw Error(STOKES_ERR_NAN, "non-finite right-hand side in an inner solve");
+    if (bb == 0.0) {
+      S.give(5);
+      return 0;
+    }
+    bn = std::sqrt(bb);
   }
-  const double bn = std::sqrt(bb);
   pre((const T*)r, (T*)z);
   copy<T>(c, d, z, n);
   int irz = 0, irzn = 1;
-  dot1<T>(c, (const T*)r, (const T*)z, n, D + irz);
+  dot1<T>(c, (const T*)r, (const T*)z, n, D + irz, kDotFast);
   int it = 0;
   bool done = false;
-  while (it < maxit) {
+  const int cap = fixed > 0 ? fixed : maxit;
+  while (it < cap) {
     op((const T*)d, (T*)q);
-    dot1<T>(c, (const T*)d, (const T*)q, n, D + 2);
+    dot1<T>(c, (const T*)d, (const T*)q, n, D + 2, kDotFast);
     cg_update<T>(c.ex, n, Coef::ratio(D + irz, D + 2), d, x, q, r);
     ++it;
-    dot1<T>(c, (const T*)r, (const T*)r, n, D + 3);
-    read_issue(c, D + 3, s + 3);
-    pre((const T*)r, (T*)z);
-    double rr = read_wait(c, s + 3);
-    if (!std::isfinite(rr)) throw Error(STOKES_ERR_NAN, "non-finite residual in an inner solve");
-    if (std::sqrt(rr) <= rtol * bn) {
-      done = true;
-      break;
+    if (fixed > 0) {
+      if (it == cap) {
+        done = true;
+        break;
+      }
+      pre((const T*)r, (T*)z);
+    } else {
+      dot1<T>(c, (const T*)r, (const T*)r, n, D + 3, kDotFast);
+      read_issue(c, D + 3, s + 3);
+      pre((const T*)r, (T*)z);
+      double rr = read_wait(c, s + 3);
+      if (!std::isfinite(rr)) throw Error(STOKES_ERR_NAN, "non-finite residual in an inner solve");
+      if (std::sqrt(rr) <= rtol * bn) {
+        done = true;
+        break;
+      }
     }
-    dot1<T>(c, (const T*)r, (const T*)z, n, D + irzn);
+    dot1<T>(c, (const T*)r, (const T*)z, n, D + irzn, kDotFast);
     axpby<T>(c.ex, n, Coef::constant(1.0), z, Coef::ratio(D + irzn, D + irz), d);
     std::swap(irz, irzn);
   }
@@ -225,7 +239,7 @@ template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
   size_t np = npres(c), nv = nvel(c);
   Tmp<T> rp(c.pool, np), z1(c.pool, np), z2(c.pool, np);
   copy<T>(c, rp, r, np);
-  project_mean<T>(c, rp, np);
+  project_mean<T>(c, rp, np, kDotFast);
   mass_inverse<T>(c, rp, z1, c.opt.mass_steps);
   const bool lumped = c.opt.schur_prec == STOKES_SCHUR_PREC_LUMPED;
   const T* linv = pick<T>(c.lumped_inv64, c.lumped_inv32);
@@ -239,15 +253,15 @@ template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
         } else {
           spmv_store<T>(c.ex, c.LQ, 1, p, y, STOKES_KERNEL_SPMV_P1);
         }
-        project_mean<T>(c, y, np);
+        project_mean<T>(c, y, np, kDotFast);
       },
       [&](const T* v, T* w) {
         Tmp<T> vp(c.pool, np);
         copy<T>(c, vp, v, np);
-        project_mean<T>(c, vp, np);
+        project_mean<T>(c, vp, np, kDotFast);
         vcycles<T>(c, 1, vp, w, 1);
       },
-      (const T*)rp, (T*)z2, c.opt.schur_inner_tol, c.opt.max_inner);
+      (const T*)rp, (T*)z2, c.opt.schur_inner_tol, c.opt.max_inner, nullptr, c.opt.schur_inner_iters);
   c.schur_inner_iters += it;
   lincomb2<T>(c.ex, np, c.mu * (1.0 + c.gamma), z1, 1.0 / c.dt, z2, z);
 }
@@ -280,7 +294,7 @@ static void method1(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
   Scalars& S = c.sc;
   const int s = S.take(6);
   double* D = S.d + s;  // 0,2: z.r (alternating) 1: d.q 3: z.r_old 4: r.r 5: beta numerator
-  dot1<T>(c, (const T*)r, (const T*)r, np, D + 4);
+  dot1<T>(c, (const T*)r, (const T*)r, np, D + 4, kDotExact);
   double rr0 = read_now(c, D + 4, s + 4);
   if (!std::isfinite(rr0)) throw Error(STOKES_ERR_NAN, "non-finite Schur right-hand side");
   if (rr0 == 0.0) {
@@ -290,14 +304,14 @@ static void method1(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
   cprec<T>(c, r, z);
   copy<T>(c, d, z, np);
   int irz = 0, irzn = 2;
-  dot1<T>(c, (const T*)z, (const T*)r, np, D + irz);
+  dot1<T>(c, (const T*)z, (const T*)r, np, D + irz, kDotExact);
   int k = 0;
   bool done = false;
   while (k < c.opt.max_outer) {
     bt_apply<T>(c.ex, c.Bt, d, t, (const T*)nullptr, (const T*)nullptr, 1.0);  // t = B^T d
     ainv<T>(c, t, wd, tol_in);                                                  // wd = A^{-1} t
     b_apply<T>(c.ex, c.B, wd, q, (const T*)nullptr, 1.0);                       // q = S d
-    dot1<T>(c, (const T*)d, (const T*)q, np, D + 1);
+    dot1<T>(c, (const T*)d, (const T*)q, np, D + 1, kDotExact);
     Coef alpha = Coef::ratio(D + irz, D + 1);
     cg_update<T>(c.ex, np, alpha, d, dP, (const T*)nullptr, (T*)nullptr);
     cg_update<T>(c.ex, nv, alpha, wd, dU, (const T*)nullptr, (T*)nullptr);
@@ -305,7 +319,7 @@ static void method1(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
     axpby<T>(c.ex, np, Coef::ratio(D + irz, D + 1, -1.0), q, Coef::constant(1.0), r);
     project_mean<T>(c, r, np);
     ++k;
-    dot1<T>(c, (const T*)r, (const T*)r, np, D + 4);
+    dot1<T>(c, (const T*)r, (const T*)r, np, D + 4, kDotExact);
     read_issue(c, D + 4, s + 4);
     cprec<T>(c, r, z);
     double rr = read_wait(c, s + 4);
@@ -318,8 +332,8 @@ static void method1(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
     const T* ys[2] = {r, rold};
     double tmp2[1];
     (void)tmp2;
-    dots<T>(c.ex, c.ds, 1, xs, ys, np, D + irzn);
-    dots<T>(c.ex, c.ds, 1, xs + 1, ys + 1, np, D + 3);
+    dots<T>(c.ex, c.ds, 1, xs, ys, np, D + irzn, kDotExact);
+    dots<T>(c.ex, c.ds, 1, xs + 1, ys + 1, np, D + 3, kDotExact);
     scalar_sub(c.ex, D + 5, D + irzn, D + 3);
     axpby<T>(c.ex, np, Coef::constant(1.0), z, Coef::ratio(D + 5, D + irz), d);
     std::swap(irz, irzn);
@@ -393,7 +407,7 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
     copy<T>(c, v0, F, nv);
     copy<T>(c, v0 + nv, rg, np);
     project_mean<T>(c, v0 + nv, np);
-    dot1<T>(c, (const T*)v0, (const T*)v0, N, D);
+    dot1<T>(c, (const T*)v0, (const T*)v0, N, D, kDotExact);
     double beta0 = std::sqrt(read_now(c, D, s));
     if (!std::isfinite(beta0)) throw Error(STOKES_ERR_NAN, "non-finite coupled right-hand side");
     double beta = beta0;
@@ -421,13 +435,13 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
             const T* xs[kMaxDots];
             const T* ys[kMaxDots];
             for (int t = 0; t < k; ++t) xs[t] = *V[i + t], ys[t] = w;
-            dots<T>(c.ex, c.ds, k, xs, ys, N, D + 2 + (pass ? m + 1 : 0) + i);
+            dots<T>(c.ex, c.ds, k, xs, ys, N, D + 2 + (pass ? m + 1 : 0) + i, kDotExact);
           }
           for (int i = 0; i <= j; ++i)
             axpby<T>(c.ex, N, Coef::ratio(D + 2 + (pass ? m + 1 : 0) + i, nullptr, -1.0), *V[i],
                      Coef::constant(1.0), w);
         }
-        dot1<T>(c, (const T*)w, (const T*)w, N, D + 1);
+        dot1<T>(c, (const T*)w, (const T*)w, N, D + 1, kDotExact);
         SK_CUDA(cudaMemcpyAsync(S.h + s + 1, D + 1, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost,
                                 c.ex.s));
         SK_CUDA(cudaStreamSynchronize(c.ex.s));
@@ -476,7 +490,7 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
       axpby<T>(c.ex, nv, Coef::constant(1.0), F, Coef::constant(-1.0), r0);
       b_apply<T>(c.ex, c.B, dU, r0 + nv, rg, -1.0);
       project_mean<T>(c, r0 + nv, np);
-      dot1<T>(c, (const T*)r0, (const T*)r0, N, D);
+      dot1<T>(c, (const T*)r0, (const T*)r0, N, D, kDotExact);
       beta = std::sqrt(read_now(c, D, s));
       if (beta <= eta * beta0) done = true;
     }

@@ -95,6 +95,19 @@ def test_mixed_precision_reaches_1e8(method, fmt):
     assert r["eu"] < 1e-5 and r["ep"] < 1e-4
 
 
+@pytest.mark.parametrize("iters,precision", [(1, 0), (3, 0), (2, 1)])
+def test_fixed_inner_iterations(iters, precision):
+    """C with a fixed number of inner PCG steps is a different (nonlinear)
+    preconditioner; the flexible outer CG still reaches the same solution."""
+    tol = 1e-12 if precision == 0 else 1e-8
+    r = run_case(8, 1e-2, 1e-3, 0.2, 2, tol=tol, precision=precision, schur_inner_iters=iters)
+    assert r["info"]["status"] == 0, r
+    if precision == 0:
+        assert r["eu"] <= PARITY and r["ep"] <= PARITY, r
+    else:
+        assert r["res"] <= 1.5e-8, r
+
+
 def test_host_api_matches_device_api():
     sk = gpu_module()
     inst, V, f = manufactured_instance(4, 0.1, 0.01, 0.2, 11)
