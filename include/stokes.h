@@ -99,6 +99,10 @@ typedef struct {
   int format;            /* 0: stencil-structured storage for A~_3, eps M_Q + L_Q,
                             M_Q, L_Q on levels with >= 2^18 rows, CSR below;
                             1: CSR everywhere; 2: stencil storage on every level */
+  int graphs;            /* 1 (default): levels >= 1 of each V-cycle are replayed
+                            from a CUDA graph captured on the context's stream
+                            at the second V-cycle (the first runs them eagerly);
+                            0: plain launches */
 } stokes_options;
 
 typedef struct {

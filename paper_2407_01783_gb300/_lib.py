@@ -38,6 +38,7 @@ class StokesOptions(C.Structure):
         ("eps_pressure", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
         ("max_refine", C.c_int), ("profile", C.c_int), ("spmv_group", C.c_int),
         ("schur_inner_iters", C.c_int), ("pass_tol", C.c_double), ("format", C.c_int),
+        ("graphs", C.c_int),
     ]
 
     def as_dict(self):

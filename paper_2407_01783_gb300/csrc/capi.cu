@@ -330,6 +330,7 @@ void stokes_default_options(stokes_options* o) {
   o->schur_inner_iters = 0;
   o->pass_tol = 3e-2;
   o->format = 0;
+  o->graphs = 1;
 }
 
 const char* stokes_status_string(int s) {
@@ -450,7 +451,11 @@ stokes_status stokes_adjoint(stokes_ctx* c, const double* dJdu, const double* dJ
 
 stokes_status stokes_destroy(stokes_ctx* c) {
   if (!c) return STOKES_OK;
-  if (c->ex.s || true) cudaStreamSynchronize(c->ex.s);
+  cudaStreamSynchronize(c->ex.s);
+  for (auto& row : c->cgraph)
+    for (auto& g : row)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->prof.reset();
   if (c->ev_read) cudaEventDestroy(c->ev_read);
   if (c->sc.h) cudaFreeHost(c->sc.h);

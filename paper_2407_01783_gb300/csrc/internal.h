@@ -47,6 +47,12 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 struct Prof {
   bool on = false;
   int only = -1;  // >= 0: CUDA events only around launches of this class (all are counted)
+  // launches recorded into a CUDA graph are counted here instead (no events)
+  struct Counts {
+    double bytes[STOKES_KERNEL_COUNT] = {};
+    int64_t launches[STOKES_KERNEL_COUNT] = {};
+  };
+  Counts* capture = nullptr;
   struct Rec {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     double bytes = 0;
@@ -378,6 +384,20 @@ struct stokes_ctx {
   // host staging for *_host calls
   double *f_dev = nullptr, *g_dev = nullptr, *u_dev = nullptr, *p_dev = nullptr;
   cudaEvent_t ev_read = nullptr;  // host reads of device scalars
+  // levels >= 1 of the V-cycle of A~_3 (which = 0) and of eps M_Q + L_Q
+  // (which = 1), FP64 [0] and FP32 [1]: fixed input/output vectors, a private
+  // vector pool for the temporaries, and the captured graph
+  struct CoarseGraph {
+    int state = 0;  // 0: next call runs eagerly, 1: next call captures, 2: replay
+    void* b = nullptr;
+    void* x = nullptr;
+    sk::VecPool pool;
+    cudaGraphExec_t exec = nullptr;
+    sk::Prof::Counts counts;
+  } cgraph[2][2];
+  // graphs are captured on this private stream (capture is not allowed on the
+  // legacy default stream) and launched on ex.s
+  cudaStream_t cap_stream = nullptr;
   // counters
   int outer_iters = 0, inner_iters = 0, schur_inner_iters = 0;
   bool outer_capped = false, inner_capped = false;

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <vector>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -103,6 +104,72 @@ template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int
 // ---------------------------------------------------------------------------
 // geometric V-cycle; which = 0: A~_3 on 3 interleaved components, 1: eps M_Q + L_Q
 // ---------------------------------------------------------------------------
+template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero);
+
+// Levels >= 1 are latency-bound (a few thousand rows per launch), so below
+// level 0 the V-cycle is replayed from a CUDA graph. Graph launches are not
+// timed per class: under per-class profiling of a class that the coarse
+// levels launch, they run eagerly instead.
+static bool coarse_graph_ok(const stokes_ctx& c, int which) {
+  if (!c.opt.graphs || c.lv.size() < 2) return false;
+  if (!c.prof.on) return true;
+  const int k = c.prof.only;
+  if (k < 0) return false;
+  const auto& G = c.cgraph[which][0].state == 2 ? c.cgraph[which][0] : c.cgraph[which][1];
+  if (G.state == 2) return G.counts.launches[k] == 0;
+  return !(k == STOKES_KERNEL_TRANSFER || k == STOKES_KERNEL_BLAS1 || k == STOKES_KERNEL_OTHER ||
+           k == (which ? STOKES_KERNEL_SPMV_P1 : STOKES_KERNEL_SPMM_A3_COARSE));
+}
+
+// swaps the context's vector pool with a graph's private one for a scope
+struct PoolSwap {
+  VecPool& a;
+  VecPool& b;
+  PoolSwap(VecPool& x, VecPool& y) : a(x), b(y) { std::swap(a.free_, b.free_); }
+  ~PoolSwap() { std::swap(a.free_, b.free_); }
+};
+
+// x_1 = V-cycle below level 0 applied to b_1 (G.b -> G.x)
+template <class T> static void coarse_run(stokes_ctx& c, int which, stokes_ctx::CoarseGraph& G) {
+  PoolSwap swap(c.pool, G.pool);
+  if (G.state == 0) {  // eager: fills the private pool with every temporary
+    vcycle<T>(c, which, 1, (const T*)G.b, (T*)G.x, true);
+    G.state = 1;
+    return;
+  }
+  if (G.state == 1) {
+    if (!c.cap_stream) SK_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    G.counts = Prof::Counts{};
+    const cudaStream_t launch = c.ex.s;
+    cudaGraph_t g = nullptr;
+    SK_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    c.prof.capture = &G.counts;
+    c.ex.s = c.cap_stream;
+    try {
+      vcycle<T>(c, which, 1, (const T*)G.b, (T*)G.x, true);
+    } catch (...) {
+      c.ex.s = launch;
+      c.prof.capture = nullptr;
+      cudaStreamEndCapture(c.cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    c.ex.s = launch;
+    c.prof.capture = nullptr;
+    SK_CUDA(cudaStreamEndCapture(c.cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    SK_CUDA(e);
+    G.state = 2;
+  }
+  SK_CUDA(cudaGraphLaunch(G.exec, c.ex.s));
+  if (c.prof.on)
+    for (int k = 0; k < STOKES_KERNEL_COUNT; ++k) {
+      c.prof.rec[k].launches += G.counts.launches[k];
+      c.prof.rec[k].bytes += G.counts.bytes[k];
+    }
+}
+
 template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero) {
   Level& L = c.lv[l];
   const int nr = which ? 1 : 3;
@@ -121,7 +188,21 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
   Level& Lc = c.lv[l + 1];
   const Csr& Mc = which ? Lc.KQ : Lc.A3;
   size_t lenc = (size_t)Mc.rows * nr;
-  {
+  if (l == 0 && coarse_graph_ok(c, which)) {
+    auto& G = c.cgraph[which][std::is_same<T, float>::value ? 1 : 0];
+    if (!G.b) {
+      G.b = c.arena.raw(lenc * sizeof(T));
+      G.x = c.arena.raw(lenc * sizeof(T));
+      G.pool.arena = &c.arena;
+    }
+    {
+      Tmp<T> r(c.pool, len);
+      spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
+      spmv_store<T>(c.ex, which ? L.R1 : L.R2, nr, r, (T*)G.b, STOKES_KERNEL_TRANSFER);
+    }
+    coarse_run<T>(c, which, G);
+    spmv_add<T>(c.ex, which ? L.P1 : L.P2, nr, (const T*)G.x, x, STOKES_KERNEL_TRANSFER);
+  } else {
     Tmp<T> r(c.pool, len);
     spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
     Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);

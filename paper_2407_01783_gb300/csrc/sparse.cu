@@ -51,6 +51,11 @@ Prof::~Prof() {
 }
 
 ProfScope::ProfScope(const Exec& e, int k, double bytes) : ex(e), kind(k) {
+  if (ex.prof && ex.prof->capture && kind >= 0) {
+    ex.prof->capture->bytes[kind] += bytes;
+    ex.prof->capture->launches[kind] += 1;
+    return;
+  }
   if (ex.prof && ex.prof->on && kind >= 0) {
     ex.prof->rec[kind].bytes += bytes;
     ex.prof->rec[kind].launches += 1;

@@ -109,3 +109,40 @@ def test_vcycle_symmetric_and_contracting(mu, dt):
     for n in (8, 16):
         sym, rate = vcycle_stats(sk, n, mu, dt, "KQ")
         assert sym < 1e-10 and rate < 0.5
+
+
+@pytest.mark.parametrize("op", ["VCYCLE_A3", "VCYCLE_KQ"])
+def test_graph_replay_matches_plain_launches(op):
+    """The coarse levels run eagerly on the first V-cycle, are captured as a
+    CUDA graph on the second and replayed afterwards; every call must give the
+    same bits as plain launches (the reductions are deterministic)."""
+    sk = gpu_module()
+    n = 12
+    V = wl.kuhn_vertices(n, 0.2, 5)
+    outs = {}
+    for graphs in (0, 1):
+        S = sk.Stokes(n, V, 0.05, 1e-3, options=sk.stokes_default_options(graphs=graphs))
+        size = 3 * S.sizes["n_inner"] if op == "VCYCLE_A3" else S.n_p1
+        r = np.random.default_rng(2).standard_normal(size)
+        outs[graphs] = [host(S.apply(op, cuda(r * (k + 1)), size)) for k in range(4)]
+        S.close()
+    for k in range(4):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_solve_with_graphs_is_bitwise_identical():
+    sk = gpu_module()
+    n = 12
+    V = wl.kuhn_vertices(n, 0.2, 6)
+    f = wl.random_force(n, 7)
+    res = []
+    for graphs in (0, 1):
+        for precision in (0, 1):
+            S = sk.Stokes(n, V, 1e-2, 1e-3, options=sk.stokes_default_options(
+                graphs=graphs, precision=precision, schur_inner_iters=2))
+            u, p, info = S.solve(cuda(f), None, 1e-9)
+            res.append((host(u), host(p), info.outer_iters))
+            S.close()
+    for a, b in ((0, 2), (1, 3)):
+        assert np.array_equal(res[a][0], res[b][0]) and np.array_equal(res[a][1], res[b][1])
+        assert res[a][2] == res[b][2]
