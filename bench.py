@@ -49,12 +49,18 @@ def workload_name(n):
     return f"kuhn{n}^3-jitter0.2-P2P1-dt1e-3-mu{{1,1e-2,1e-4}}-schurCG-CLambda"
 
 
+INNER_ITERS = 2
+
+
 def config(n, precision):
     return {"workload": workload_name(n), "n_cubes": n, "mus": list(MUS), "dt": DT,
             "jitter": JITTER, "seed": SEED, "tol": TOL, "precision": precision,
             "dofs_per_solve": 3 * (2 * n + 1) ** 3 + (n + 1) ** 3,
             "solves_per_step": len(MUS), "method": "schur-cg", "schur_prec": "C^Lambda",
             "velocity_prec": "A~_3, 1 V-cycle (Chebyshev-Jacobi degree 2)",
+            "schur_inner": ("fixed %d PCG iterations on B Lambda^-1 B^T (1 V-cycle of M_Q + L_Q)" % INNER_ITERS
+                            if INNER_ITERS > 0 else "PCG on B Lambda^-1 B^T to rel. 1e-1"),
+            "coarse_levels": "replayed from captured CUDA graphs",
             "l2": "inputs larger than L2 (every matrix > 129 MB), no flush",
             "parallelism": "replicas"}
 
@@ -381,6 +387,10 @@ def run_ours(args):
     if not args.no_batched:
         batched = run_batched(sk, torch, wl, dev, world, dist)
 
+    coupled96 = None
+    if not args.no_coupled96:
+        coupled96 = run_coupled96(sk, torch, wl, dev, world, dist)
+
     if rank != 0:
         return None
     cpu = run_cpu_baseline(1) if (world == 1 and not args.no_cpu) else None
@@ -404,6 +414,7 @@ def run_ours(args):
         "plain_fp64": fp64,
         "method2_coupled": coupled,
         "batched": batched,
+        "coupled_96": coupled96,
     }
     return line
 
@@ -429,6 +440,40 @@ def run_batched(sk, torch, wl, dev, world, dist, count=32, rhs=4):
             "worst_residual": max(x["rel_residual"] for x in flat),
             "failed": sum(1 for x in flat if x["status"] != 0),
             "scheme": "one context + stream per instance, host thread per instance, mixed precision"}
+
+
+def run_coupled96(sk, torch, wl, dev, world, dist, n=96, mu=1e-3, dt=1e-3, gammas=(0.0, 1.0, 10.0)):
+    """Fully coupled form on the 96^3 jittered mesh: block-triangular FGMRES(30)
+    vs the Schur form, mixed precision, for each augmented-Lagrangian gamma.
+    One untimed solve, then one solve timed with CUDA events, per case."""
+    V = wl.kuhn_vertices(n, JITTER, SEED)
+    f = torch.as_tensor(wl.manufactured_force(n, V, mu, dt, SEED), device=dev)
+    dofs = 3 * (2 * n + 1) ** 3 + (n + 1) ** 3
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"kuhn{n}^3-jitter0.2-P2P1-dt1e-3-mu1e-3-gamma{{0,1,10}}", "mu": mu, "dt": dt,
+           "dofs": dofs, "cases": []}
+    for gamma in gammas:
+        for label, extra in (("fgmres_block_triangular", dict(method=sk.METHOD_COUPLED, block_lu=0)),
+                             ("schur_cg", dict(method=sk.METHOD_SCHUR))):
+            opt = sk.stokes_default_options(precision=sk.PRECISION_MIXED, vcycles=1, **extra)
+            S = sk.Stokes(n, V, mu, dt, gamma, opt, device=dev)
+            u = torch.empty_like(f)
+            p = torch.empty(S.n_p1, dtype=torch.float64, device=dev)
+            S.solve(f, None, TOL, out=(u, p))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, info = S.solve(f, None, TOL, out=(u, p))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+            S.close()
+            out["cases"].append({"gamma": gamma, "method": label, "ms": ms,
+                                 "value": world * dofs / (ms / 1e3), "unit": UNIT,
+                                 "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
+                                 "refinements": info.refinements, "rel_residual": info.rel_residual,
+                                 "status": info.status})
+    return out
 
 
 def run_reference(args):
@@ -474,6 +519,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-coupled", action="store_true", help="skip the Method 2 (coupled FGMRES) line")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch line")
+    ap.add_argument("--no-coupled96", action="store_true", help="skip the 96^3 coupled-vs-Schur comparison")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
     ap.add_argument("--schur-inner-iters", type=int, default=2,
@@ -485,6 +531,8 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    global INNER_ITERS
+    INNER_ITERS = args.schur_inner_iters
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)

@@ -89,9 +89,10 @@ typedef struct {
                             events; 2 + k: count all, time only class k
                             (STOKES_KERNEL_*); 0: off */
   int spmv_group;        /* threads per sparse row: 0 autotune, else 1..32 */
-  int schur_inner_iters; /* > 0: the solve inside C runs exactly this many PCG
-                            iterations with no convergence test (no host
-                            synchronisation); 0: stop at schur_inner_tol */
+  int schur_inner_iters; /* > 0 (default 2): the solve inside C runs exactly this
+                            many PCG iterations with no convergence test (no
+                            host synchronisation; the outer CG is flexible);
+                            0: stop at schur_inner_tol */
   double pass_tol;       /* mixed precision: relative reduction asked of each FP32
                             correction pass (outer Krylov tolerance per pass);
                             its inner velocity solves get max(inner_tol,

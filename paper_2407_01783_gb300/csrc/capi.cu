@@ -327,7 +327,7 @@ void stokes_default_options(stokes_options* o) {
   o->max_refine = 6;
   o->profile = 0;
   o->spmv_group = 0;
-  o->schur_inner_iters = 0;
+  o->schur_inner_iters = 2;
   o->pass_tol = 3e-2;
   o->format = 0;
   o->graphs = 1;

@@ -98,3 +98,75 @@ def test_autograd_function():
     assert rel_err(host(ft.grad), host(dJdf)) < 1e-10
     assert abs(float(mu_t.grad) - dmu) < 1e-10 * abs(dmu)
     S.close()
+
+
+def interior_index(n):
+    """All-node indices of the (2n-1)^3 interior P2 nodes, x fastest."""
+    N = 2 * n + 1
+    q = np.arange(1, 2 * n)
+    K, Jj, I = np.meshgrid(q, q, q, indexing="ij")
+    return (I + N * (Jj + N * K)).ravel()
+
+
+def test_adjoint_64_tracking_functional_finite_differences():
+    torch = pytest.importorskip("torch")
+    """64^3 jittered mesh, J = 1/2 ||u - u_t||^2_M with a seeded smooth target
+    u_t that vanishes on the boundary (so dJ/dU = M_V (u - u_t) on interior
+    rows). Gradients dJ/df and dJ/dmu through StokesSolve (autograd, mixed
+    precision: FP32 inner, FP64 outer) against central differences with step
+    1e-6 on 16 seeded smooth directions. J is quadratic in f, so the central
+    difference has no truncation error; what remains is the solver tolerance
+    (1e-11) divided by the step, hence the bar of 1e-4 relative to |dJ/df||v|."""
+    sk = gpu_module()
+    n, mu, dt, tol = 64, 1e-2, 1e-3, 1e-11
+    V = wl.kuhn_vertices(n, 0.2, 64)
+    X = wl.p2_node_coords(V, n)
+    f = wl.manufactured_force(n, V, mu, dt, 64)
+    ut = wl.Manufactured(65).velocity(X)
+    inner = interior_index(n)
+    boundary = np.setdiff1d(np.arange(X.shape[0]), inner)
+    assert np.abs(ut[boundary]).max() < 1e-12
+    opt = sk.stokes_default_options(precision=1, vcycles=1)
+    S = sk.Stokes(n, V, mu, dt, 0.0, opt)
+    ni = inner.size
+    inner_t = torch.as_tensor(inner, device="cuda")
+    ut_t = cuda(ut)
+
+    def mass_times(Sx, e):                  # (M_V e) on interior rows, node-interleaved
+        return Sx.apply("LOAD", e.reshape(-1), 3 * ni).reshape(3, ni).T
+
+    def J_of(Sx, fx):
+        u, _, info = Sx.solve(cuda(fx), None, tol)
+        assert info.status == 0
+        e = u - ut_t
+        return 0.5 * float((e[inner_t] * mass_times(Sx, e)).sum())
+
+    # gradient through the autograd wrapper: the loss u . w with w = M_V (u - u_t)
+    # fixed has the same derivative in f and mu as J at this point
+    ft = torch.tensor(f, device="cuda", requires_grad=True)
+    mu_t = torch.tensor(mu, dtype=torch.float64, device="cuda", requires_grad=True)
+    u, p = sk.StokesSolve.apply(S, ft, mu_t, tol)
+    w = torch.zeros_like(u)
+    w[inner_t] = mass_times(S, (u - ut_t).detach())
+    (u * w).sum().backward()
+    g = host(ft.grad)
+    dmu = float(mu_t.grad)
+    gnorm = np.linalg.norm(g)
+    h = 1e-6
+    fscale = np.linalg.norm(f)
+    for k in range(16):
+        v = wl.Manufactured(1000 + k).body_force(X, mu, dt)
+        v *= fscale / np.linalg.norm(v)
+        fd = (J_of(S, f + h * v) - J_of(S, f - h * v)) / (2 * h)
+        an = float((g * v).sum())
+        assert abs(fd - an) <= 1e-4 * gnorm * np.linalg.norm(v), (k, fd, an)
+    S.close()
+    hm = 1e-6 * mu
+    Sp = sk.Stokes(n, V, mu + hm, dt, 0.0, opt)
+    Jp = J_of(Sp, f)
+    Sp.close()
+    Sm = sk.Stokes(n, V, mu - hm, dt, 0.0, opt)
+    Jm = J_of(Sm, f)
+    Sm.close()
+    fd_mu = (Jp - Jm) / (2 * hm)
+    assert abs(fd_mu - dmu) <= 1e-3 * abs(dmu), (fd_mu, dmu)

@@ -88,14 +88,16 @@ def test_one_level_vcycle_is_exact_inverse():
     S.close()
 
 
-def test_largest_configuration_coupled_96():
-    """96^3 jittered mesh (22.5 M DOFs), Method 2, mixed precision: the largest
-    configuration solves to 1e-8."""
+@pytest.mark.parametrize("gamma", [0.0, 1.0, 10.0])
+def test_largest_configuration_coupled_96(gamma):
+    """96^3 jittered mesh (22.5 M DOFs), block-triangular FGMRES(30) on the
+    coupled system with augmented Lagrangian gamma, mixed precision: the
+    largest configuration solves to 1e-8."""
     sk = gpu_module()
     n, mu, dt = 96, 1e-3, 1e-3
     V = wl.kuhn_vertices(n, 0.2, 3)
     f = wl.manufactured_force(n, V, mu, dt, 3)
-    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1, method=1))
+    S = sk.Stokes(n, V, mu, dt, gamma, sk.stokes_default_options(precision=1, vcycles=1, method=1, block_lu=0))
     assert S.sizes["dofs"] == 21567171 + 912673
     u, p, info = S.solve(cuda(f), None, 1e-8)
     assert info.status == 0 and info.rel_residual <= 1e-8, info.as_dict()
