@@ -179,11 +179,18 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+def kernel_source_sha():
+    """Hash of the files that define the sparse kernels (sparse.cu, internal.h)."""
+    h = hashlib.sha256()
+    for name in ("sparse.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2407_01783_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel_name):
     """Per-launch DRAM bytes of `kernel_name` from a committed ncu summary, if the
     summary was taken on the current kernel source."""
-    src = os.path.join(ROOT, "paper_2407_01783_gb300", "csrc", "sparse.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     prof = os.path.join(ROOT, "profiles")
     if not os.path.isdir(prof):
         return None
@@ -442,15 +449,15 @@ def run_batched(sk, torch, wl, dev, world, dist, count=32, rhs=4):
             "scheme": "one context + stream per instance, host thread per instance, mixed precision"}
 
 
-def run_coupled96(sk, torch, wl, dev, world, dist, n=96, mu=1e-3, dt=1e-3, gammas=(0.0, 1.0, 10.0)):
+def run_coupled96(sk, torch, wl, dev, world, dist, n=96, mu=1e-3, dt=1e-3, gammas=(0.0, 1.0, 10.0), seed=3):
     """Fully coupled form on the 96^3 jittered mesh: block-triangular FGMRES(30)
     vs the Schur form, mixed precision, for each augmented-Lagrangian gamma.
     One untimed solve, then one solve timed with CUDA events, per case."""
-    V = wl.kuhn_vertices(n, JITTER, SEED)
-    f = torch.as_tensor(wl.manufactured_force(n, V, mu, dt, SEED), device=dev)
+    V = wl.kuhn_vertices(n, JITTER, seed)
+    f = torch.as_tensor(wl.manufactured_force(n, V, mu, dt, seed), device=dev)
     dofs = 3 * (2 * n + 1) ** 3 + (n + 1) ** 3
     stream = torch.cuda.current_stream(dev)
-    out = {"workload": f"kuhn{n}^3-jitter0.2-P2P1-dt1e-3-mu1e-3-gamma{{0,1,10}}", "mu": mu, "dt": dt,
+    out = {"workload": f"kuhn{n}^3-jitter0.2-P2P1-dt1e-3-mu1e-3-gamma{{0,1,10}}", "seed": seed, "mu": mu, "dt": dt,
            "dofs": dofs, "cases": []}
     for gamma in gammas:
         for label, extra in (("fgmres_block_triangular", dict(method=sk.METHOD_COUPLED, block_lu=0)),

@@ -110,7 +110,7 @@ def interior_index(n):
 
 def test_adjoint_64_tracking_functional_finite_differences():
     torch = pytest.importorskip("torch")
-    """64^3 jittered mesh, J = 1/2 ||u - u_t||^2_M with a seeded smooth target
+    """64^3 jittered mesh (seed 5), J = 1/2 ||u - u_t||^2_M with a seeded smooth target
     u_t that vanishes on the boundary (so dJ/dU = M_V (u - u_t) on interior
     rows). Gradients dJ/df and dJ/dmu through StokesSolve (autograd, mixed
     precision: FP32 inner, FP64 outer) against central differences with step
@@ -119,9 +119,9 @@ def test_adjoint_64_tracking_functional_finite_differences():
     (1e-11) divided by the step, hence the bar of 1e-4 relative to |dJ/df||v|."""
     sk = gpu_module()
     n, mu, dt, tol = 64, 1e-2, 1e-3, 1e-11
-    V = wl.kuhn_vertices(n, 0.2, 64)
+    V = wl.kuhn_vertices(n, 0.2, 5)
     X = wl.p2_node_coords(V, n)
-    f = wl.manufactured_force(n, V, mu, dt, 64)
+    f = wl.manufactured_force(n, V, mu, dt, 5)
     ut = wl.Manufactured(65).velocity(X)
     inner = interior_index(n)
     boundary = np.setdiff1d(np.arange(X.shape[0]), inner)

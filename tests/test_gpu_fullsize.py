@@ -70,3 +70,18 @@ def test_bench_workload_method2_mixed(workload48):
     est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=7)
     assert est <= 2 * TOL, est
     S.close()
+
+
+def test_bench_workload_random_rhs(workload48):
+    """The 48^3 workload with an N(0, 1) nodal body force (seed 2) instead of the
+    manufactured one: rough right-hand side, same tolerance, sampled rows."""
+    sk = gpu_module()
+    n, V, mus, dt, mesh = workload48
+    mu = 1e-2
+    f = wl.random_force(n, 2)
+    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1))
+    u, p, info = S.solve(cuda(f), None, TOL)
+    assert info.status == 0 and info.rel_residual <= TOL
+    est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=11)
+    assert est <= 2 * TOL, est
+    S.close()
