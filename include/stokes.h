@@ -184,8 +184,12 @@ typedef enum {
   STOKES_OP_PROLONG_P2 = 13,  /* y(level) = P x(level+1), 3 components         */
   STOKES_OP_RESTRICT_P2 = 14, /* y(level+1) = P^T x(level)                     */
   STOKES_OP_PROLONG_P1 = 15,  /* y(level) = P x(level+1)                       */
-  STOKES_OP_LOAD = 16         /* y = M_V f on interior rows, x = nodal f on all
+  STOKES_OP_LOAD = 16,        /* y = M_V f on interior rows, x = nodal f on all
                                  nodes [(2n+1)^3][3] (node-interleaved)       */
+  STOKES_OP_A_DF = 17         /* y = A x as the mixed-precision refinement
+                                 residual computes it: FP32 hi/lo pairs of A
+                                 and x, exact FP32 products, double-float sums
+                                 (mixed-precision contexts only)              */
 } stokes_op;
 
 stokes_status stokes_apply(stokes_ctx* ctx, int op, int level, const double* x, double* y);

@@ -23,7 +23,7 @@ PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 OP = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED_INV=7, VCYCLE_A3=8, VCYCLE_KQ=9,
           SCHUR_PREC=10, SCHUR=11, AGAMMA=12, PROLONG_P2=13, RESTRICT_P2=14, PROLONG_P1=15,
-          LOAD=16)
+          LOAD=16, A_DF=17)
 MAT = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED=7)
 KERNEL = dict(SPMM_A3=0, SPMV_A=1, B=2, BT=3, SPMV_P1=4, TRANSFER=5, BLAS1=6, OTHER=7,
               SPMM_A3_COARSE=8, RESIDUAL=9)

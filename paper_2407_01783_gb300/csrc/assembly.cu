@@ -944,6 +944,18 @@ void to_f32(const Exec& ex, const double* src, float* dst, size_t n) {
   SK_CHECK_LAUNCH();
 }
 
+__global__ void k_to_f32_lo(const double* __restrict__ s, const float* __restrict__ hi, float* __restrict__ lo,
+                            size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    lo[i] = (float)(s[i] - (double)hi[i]);
+}
+
+void to_f32_lo(const Exec& ex, const double* src, const float* hi, float* lo, size_t n) {
+  if (!n) return;
+  k_to_f32_lo<<<(unsigned)std::min<size_t>(cdiv(n, 256), 1 << 20), 256, 0, ex.s>>>(src, hi, lo, n);
+  SK_CHECK_LAUNCH();
+}
+
 // Coarse-level geometry: coarse vertex i sits at logical position i/nc; its
 // coordinates are the P1 interpolation of the fine (jittered) vertex
 // positions at that logical point on the fine Kuhn mesh. For nf = 2 nc this is

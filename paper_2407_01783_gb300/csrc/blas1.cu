@@ -5,6 +5,8 @@
 // waits for a dot product it does not need to see.
 #include <cmath>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace sk {
@@ -290,6 +292,23 @@ __global__ void k_nonfinite(size_t n, const double* __restrict__ x, int* flag) {
   SK_IDX;
   if (!isfinite(x[i])) atomicOr(flag, 2);
 }
+__global__ void k_split_f64(size_t n, const double* __restrict__ x, float* __restrict__ hi,
+                            float* __restrict__ lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+}
+
+void split_f64(const Exec& ex, size_t n, const double* x, float* hi, float* lo) {
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, 16.0 * n);
+  k_split_f64<<<(unsigned)std::min<size_t>(cdiv(n, 256), 1 << 20), 256, 0, ex.s>>>(n, x, hi, lo);
+  SK_CHECK_LAUNCH();
+}
+
 void count_nonfinite(const Exec& ex, size_t n, const double* x, int* flag) {
   if (!n) return;
   ProfScope ps(ex, STOKES_KERNEL_OTHER, 8.0 * n);

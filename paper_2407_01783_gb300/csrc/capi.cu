@@ -235,6 +235,8 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   c.P_last = c.arena.alloc<double>(L0.np);
   if (c.mixed) {
     c.A.v32 = f32_copy(c, c.A.v64, 9 * (size_t)c.A.nnz);
+    c.A.v32lo = c.arena.alloc<float>(9 * (size_t)c.A.nnz);
+    to_f32_lo(c.ex, c.A.v64, c.A.v32, c.A.v32lo, 9 * (size_t)c.A.nnz);
     c.B.v32 = f32_copy(c, c.B.v64, 3 * (size_t)c.B.nnz);
     c.Bt.v32 = f32_copy(c, c.Bt.v64, 3 * (size_t)c.Bt.nnz);
     c.MQ.v32 = f32_copy(c, c.MQ.v64, c.MQ.nnz);

@@ -165,6 +165,7 @@ struct Csr {
   int* col = nullptr;
   double* v64 = nullptr;
   float* v32 = nullptr;
+  float* v32lo = nullptr;  // v64 - v32 rounded to FP32 (double-float residual), or null
   int group = 8;  // threads per row
   const StencilOp* st = nullptr;  // same matrix in stencil storage (used when set)
   template <class T> T* v() const;
@@ -281,6 +282,8 @@ void diag_inverse(const Exec& ex, const Csr& m, double* dinv);
 // level size n, values copied from the assembled CSR m (FP64; FP32 on request).
 StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int p2, int n, const Csr& m);
 void to_f32(const Exec& ex, const double* src, float* dst, size_t n);
+// lo = FP32(src - hi): with hi = FP32(src), hi + lo carries src to ~2^-48
+void to_f32_lo(const Exec& ex, const double* src, const float* hi, float* lo, size_t n);
 void subsample_vertices(int nf, int nc, const double* Xf_host, double* Xc_host);
 
 // ---------------------------------------------------------------------------
@@ -303,6 +306,12 @@ template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* 
 template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha);
 template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* scale,
                                  const T* b, double alpha);
+// y = b - A x for the BSR3 matrix in double-float arithmetic: A = v32 + v32lo,
+// x = xh + xl (both FP32 pairs), exact FP32 products (FMA TwoProduct) summed
+// with TwoSum; y and b FP64. Relative error ~1e-13 of |A||x| using FP32 units
+// only (FP64 throughput is a small fraction of FP32 on this GPU).
+void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y,
+                      int kind);
 template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y);
 void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
 
@@ -345,6 +354,8 @@ template <class T> void sub_ratio(const Exec& ex, size_t n, const double* num, c
 template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* dinv, const T* b,
                                    double c, T* d, T* x);
 template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D* y);
+// hi = FP32(x), lo = FP32(x - hi)
+void split_f64(const Exec& ex, size_t n, const double* x, float* hi, float* lo);
 template <class S, class D> void add_convert(const Exec& ex, size_t n, const S* x, D* y);
 void expand_velocity(const Exec& ex, int n, const double* ured, double* uall);
 void restrict_velocity(const Exec& ex, int n, const double* uall, double* ured);

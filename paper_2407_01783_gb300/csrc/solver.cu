@@ -618,7 +618,14 @@ static void correction(stokes_ctx& c, const double* rF, const double* rg, double
 static double full_residual(stokes_ctx& c, const double* F, const double* g, const double* U, const double* P,
                             double* rF, double* rg, double normFg) {
   const size_t nv = nvel(c), np = npres(c);
-  bsr3_apply<double>(c.ex, c.A, U, rF, F, STOKES_KERNEL_RESIDUAL);
+  if (c.A.v32lo) {
+    // mixed precision: the same FP64-accurate product on FP32 units
+    Tmp<float> uh(c.pool, nv), ul(c.pool, nv);
+    split_f64(c.ex, nv, U, uh, ul);
+    bsr3_residual_df(c.ex, c.A, uh, ul, F, rF, STOKES_KERNEL_RESIDUAL);
+  } else {
+    bsr3_apply<double>(c.ex, c.A, U, rF, F, STOKES_KERNEL_RESIDUAL);
+  }
   bt_apply<double>(c.ex, c.Bt, P, rF, (const double*)nullptr, rF, 1.0);
   b_apply<double>(c.ex, c.B, U, rg, g, -1.0);
   const int s = c.sc.take(2);
@@ -835,6 +842,17 @@ void apply_operator(stokes_ctx* cp, int op, int level, const double* x, double* 
       spmv_store<double>(c.ex, L.P1, 1, x, y, STOKES_KERNEL_TRANSFER);
       break;
     case STOKES_OP_LOAD: assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, x, y); break;
+    case STOKES_OP_A_DF: {
+      SK_REQUIRE(c.A.v32lo, STOKES_ERR_ARG, "double-float A needs a mixed-precision context");
+      Tmp<float> xh(c.pool, nv), xl(c.pool, nv);
+      Tmp<double> zero_b(c.pool, nv);
+      zero<double>(c, zero_b, nv);
+      split_f64(c.ex, nv, x, xh, xl);
+      Tmp<double> t(c.pool, nv);
+      bsr3_residual_df(c.ex, c.A, xh, xl, zero_b, t, STOKES_KERNEL_RESIDUAL);  // t = -A x
+      scale_copy<double>(c.ex, nv, Coef::constant(-1.0), t, y);
+      break;
+    }
     default: throw Error(STOKES_ERR_ARG, "unknown operator");
   }
   (void)np;

@@ -240,6 +240,118 @@ __global__ void __launch_bounds__(256) k_bsr3(int rows, const int* __restrict__ 
   if (row < rows && lane == 0) epi(row, acc);
 }
 
+// ---------------------------------------------------------------------------
+// double-float BSR3 residual. Error-free transformations (published methods):
+// TwoProduct with an FMA, p + e = a * b exactly (Ogita, Rump & Oishi 2005);
+// TwoSum, s + e = a + b exactly (Knuth, TAOCP vol. 2, 4.2.2). The _rn
+// intrinsics keep the compiler from contracting these steps into FMAs.
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+// s += (ah + al) * (xh + xl), dropping al * xl (2^-48 relative)
+__device__ __forceinline__ void df_madd(DF& s, float ah, float al, float xh, float xl) {
+  const float ph = __fmul_rn(ah, xh);
+  const float pe = __fmaf_rn(ah, xh, -ph);
+  const float pc = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
+  const float t = __fadd_rn(s.h, ph);
+  const float z = __fsub_rn(t, s.h);
+  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  s.h = t;
+  s.l = __fadd_rn(s.l, __fadd_rn(e, __fadd_rn(pe, pc)));
+}
+__device__ __forceinline__ void df_add(DF& s, float oh, float ol) {
+  const float t = __fadd_rn(s.h, oh);
+  const float z = __fsub_rn(t, s.h);
+  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(oh, z));
+  s.h = t;
+  s.l = __fadd_rn(s.l, __fadd_rn(ol, e));
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_bsr3_df(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                                                 const float* __restrict__ vh, const float* __restrict__ vl,
+                                                 long long nnz, const float* __restrict__ xh,
+                                                 const float* __restrict__ xl, size_t xs,
+                                                 const double* __restrict__ b, double* __restrict__ y) {
+  constexpr int U = 2;
+  int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = gt / G, lane = gt & (G - 1);
+  DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  if (row < rows) {
+    const int e = rp[row + 1];
+    for (int k = rp[row] + lane; k < e; k += U * G) {
+      int c[U];
+      float ah[U][9], al[U][9];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kk = k + u * G;
+        const bool ok = kk < e;
+        const int ks = ok ? kk : e - 1;  // in-bounds re-read, zero contribution
+        c[u] = col[ks];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          const float h = vh[(size_t)j * nnz + ks], l = vl[(size_t)j * nnz + ks];
+          ah[u][j] = ok ? h : 0.f;
+          al[u][j] = ok ? l : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float x_h[3], x_l[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          x_h[q] = xh[q * xs + c[u]];
+          x_l[q] = xl[q * xs + c[u]];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) df_madd(acc[r], ah[u][3 * r + q], al[u][3 * r + q], x_h[q], x_l[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float oh = __shfl_xor_sync(0xffffffffu, acc[r].h, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, acc[r].l, o);
+      df_add(acc[r], oh, ol);
+    }
+  if (row < rows && lane == 0) {
+    const size_t ns = (size_t)rows;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) y[r * ns + row] = b[r * ns + row] - ((double)acc[r].h + (double)acc[r].l);
+  }
+}
+
+template <int G>
+static void launch_bsr3_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b,
+                           double* y) {
+  const int bs = 256;
+  const int grid = cdiv((long long)m.rows * G, bs);
+  if (grid == 0) return;
+  k_bsr3_df<G><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v32, m.v32lo, m.nnz, xh, xl, m.cols, b, y);
+  SK_CHECK_LAUNCH();
+}
+
+void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y,
+                      int kind) {
+  SK_REQUIRE(m.v32 && m.v32lo && m.br == 3 && m.bc == 3, STOKES_ERR_ARG, "double-float residual needs A hi/lo");
+  // matrix hi+lo planes, column indices, x hi+lo gathered once, b read, y written
+  ProfScope ps(ex, kind, (double)m.nnz * (4.0 + 8.0 * 9) + 4.0 * (m.rows + 1) + 8.0 * 3 * m.cols +
+                             16.0 * 3 * m.rows);
+  switch (m.group) {
+    case 1: launch_bsr3_df<1>(ex, m, xh, xl, b, y); break;
+    case 2: launch_bsr3_df<2>(ex, m, xh, xl, b, y); break;
+    case 4: launch_bsr3_df<4>(ex, m, xh, xl, b, y); break;
+    case 8: launch_bsr3_df<8>(ex, m, xh, xl, b, y); break;
+    case 16: launch_bsr3_df<16>(ex, m, xh, xl, b, y); break;
+    default: launch_bsr3_df<32>(ex, m, xh, xl, b, y); break;
+  }
+}
+
 // 1x3 blocks: B (P1 rows, interior P2 node columns)
 template <int G, class T, class Epi>
 __global__ void __launch_bounds__(256) k_b(int rows, const int* __restrict__ rp, const int* __restrict__ col,

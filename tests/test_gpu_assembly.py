@@ -140,3 +140,24 @@ def test_augmented_operator_matches_definition():
     ref = orc.A @ x + gamma * 0.5 * (orc.B.T @ spla.spsolve(orc.MQ.tocsc(), orc.B @ x))
     assert rel_err(aos(host(S.apply("AGAMMA", cuda(soa(x)), x.size))), ref) < 1e-8
     S.close()
+
+
+def test_double_float_residual_product():
+    """The mixed-precision refinement residual forms A U from FP32 hi/lo pairs
+    with exact FP32 products and double-float sums. Each row must match the
+    FP64 product within 1e-12 of sum_j |A_ij||x_j| (the error analysis gives
+    ~k^2 2^-48 for k products per lane; a plain FP32 product misses by ~1e-7,
+    so the bound discriminates)."""
+    sk = gpu_module()
+    n, mu, dt = 6, 0.05, 2e-3
+    V = wl.kuhn_vertices(n, 0.2, 17)
+    orc = StokesSystem(KuhnMesh(n, V), mu, dt)
+    S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1))
+    x = np.random.default_rng(5).standard_normal(orc.A.shape[0])
+    y = aos(host(S.apply("A_DF", cuda(soa(x)), x.size)))
+    ref = orc.A @ x
+    scale = abs(orc.A) @ abs(x)
+    err = float(np.max(np.abs(y - ref) / scale))
+    print("double-float product: max error / (|A||x|) =", err)
+    assert err <= 1e-12
+    S.close()
