@@ -44,25 +44,61 @@ __global__ void __launch_bounds__(256) k_dots(DotArgs<T> a) {
     // per-thread sums of FP32 vectors stay in FP32 with Neumaier's compensated
     // summation (error ~ eps_32 per product, not per partial sum); only the
     // cross-thread reduction is FP64.
-    float fs[K], fc[K];
+    // four independent accumulators per dot keep four loads per vector in
+    // flight per thread
+    float fs[K][4], fc[K][4];
 #pragma unroll
-    for (int j = 0; j < K; ++j) fs[j] = 0.f, fc[j] = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) fs[j][u] = 0.f, fc[j][u] = 0.f;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < a.n; i += 4 * stride) {
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        float p = (float)a.x[j][i] * (a.y[j] ? (float)a.y[j][i] : 1.f);
-        float t = fs[j] + p;
-        fc[j] += fabsf(fs[j]) >= fabsf(p) ? (fs[j] - t) + p : (p - t) + fs[j];
-        fs[j] = t;
+        float p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = (float)a.x[j][i + u * stride] * (a.y[j] ? (float)a.y[j][i + u * stride] : 1.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float t = fs[j][u] + p[u];
+          fc[j][u] += fabsf(fs[j][u]) >= fabsf(p[u]) ? (fs[j][u] - t) + p[u] : (p[u] - t) + fs[j][u];
+          fs[j][u] = t;
+        }
+      }
+    }
+    for (; i < a.n; i += stride) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const float p = (float)a.x[j][i] * (a.y[j] ? (float)a.y[j][i] : 1.f);
+        const float t = fs[j][0] + p;
+        fc[j][0] += fabsf(fs[j][0]) >= fabsf(p) ? (fs[j][0] - t) + p : (p - t) + fs[j][0];
+        fs[j][0] = t;
       }
     }
 #pragma unroll
-    for (int j = 0; j < K; ++j) s[j] = (double)fs[j] + (double)fc[j];
-  } else {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    for (int j = 0; j < K; ++j)
 #pragma unroll
-      for (int j = 0; j < K; ++j) s[j] += (double)a.x[j][i] * (a.y[j] ? (double)a.y[j][i] : 1.0);
+      for (int u = 0; u < 4; ++u) s[j] += (double)fs[j][u] + (double)fc[j][u];
+  } else {
+    double t[K][4];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[j][u] = 0.0;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < a.n; i += 4 * stride) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          t[j][u] += (double)a.x[j][i + u * stride] * (a.y[j] ? (double)a.y[j][i + u * stride] : 1.0);
     }
+    for (; i < a.n; i += stride) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) t[j][0] += (double)a.x[j][i] * (a.y[j] ? (double)a.y[j][i] : 1.0);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) s[j] = (t[j][0] + t[j][1]) + (t[j][2] + t[j][3]);
   }
   __shared__ double sh[K][8];
   __shared__ bool last;
@@ -125,10 +161,14 @@ void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const 
   SK_CHECK_LAUNCH();
 }
 
-#define SK_GRID(n) cdiv((long long)(n), 256), 256, 0, ex.s
-#define SK_IDX                                              \
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; \
-  if (i >= n) return;
+// Elementwise kernels run a grid-stride loop over at most kEwBlocks blocks
+// (8 resident 256-thread blocks per SM): a block's coefficient prologue is paid
+// once per ~8 elements per thread rather than once per 256 elements.
+constexpr int kEwBlocks = 8 * 152;
+static inline int ew_grid(size_t n) { return (int)std::min<long long>(cdiv((long long)n, 256), kEwBlocks); }
+#define SK_GRID(n) ew_grid(n), 256, 0, ex.s
+#define SK_LOOP(i) \
+  _Pragma("unroll 4") for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
 
 // Coefficients from device scalars are evaluated once per block (one FP64
 // division per block instead of per element: GB300's FP64 rate is low).
@@ -144,9 +184,12 @@ void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const 
 template <class T>
 __global__ void k_axpby(size_t n, Coef a, const T* __restrict__ x, Coef b, T* __restrict__ y) {
   SK_COEF2(a, b, ad, bd);
-  SK_IDX;
   const T av = (T)ad, bv = (T)bd;
-  y[i] = av * x[i] + (bv == T(0) ? T(0) : bv * y[i]);
+  if (bv == T(0)) {
+    SK_LOOP(i) { y[i] = av * x[i]; }
+  } else {
+    SK_LOOP(i) { y[i] = av * x[i] + bv * y[i]; }
+  }
 }
 template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y) {
   if (!n) return;
@@ -160,11 +203,17 @@ __global__ void k_cg_update(size_t n, Coef a, const T* __restrict__ d, T* __rest
                             T* __restrict__ r, int* flag) {
   SK_COEF2(a, a, ad, unused);
   (void)unused;
-  SK_IDX;
-  if (i == 0 && flag && a.den && !(*a.den > 0.0)) atomicOr(flag, 1);  // p^T A p <= 0: breakdown
+  if (blockIdx.x == 0 && threadIdx.x == 0 && flag && a.den && !(*a.den > 0.0))
+    atomicOr(flag, 1);  // p^T A p <= 0: breakdown
   const T av = (T)ad;
-  x[i] += av * d[i];
-  if (r) r[i] -= av * q[i];
+  if (r) {
+    SK_LOOP(i) {
+      x[i] += av * d[i];
+      r[i] -= av * q[i];
+    }
+  } else {
+    SK_LOOP(i) { x[i] += av * d[i]; }
+  }
 }
 template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r) {
   if (!n) return;
@@ -176,8 +225,9 @@ template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, 
 template <class T> __global__ void k_scale_copy(size_t n, Coef a, const T* __restrict__ x, T* __restrict__ y) {
   SK_COEF2(a, a, ad, unused);
   (void)unused;
-  SK_IDX;
-  y[i] = (T)ad * x[i];
+  SK_LOOP(i) {
+    y[i] = (T)ad * x[i];
+  }
 }
 template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x, T* y) {
   if (!n) return;
@@ -188,8 +238,9 @@ template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x,
 
 template <class T>
 __global__ void k_lincomb2(size_t n, T c1, const T* __restrict__ x1, T c2, const T* __restrict__ x2, T* __restrict__ y) {
-  SK_IDX;
-  y[i] = c1 * x1[i] + c2 * x2[i];
+  SK_LOOP(i) {
+    y[i] = c1 * x1[i] + c2 * x2[i];
+  }
 }
 template <class T> void lincomb2(const Exec& ex, size_t n, double c1, const T* x1, double c2, const T* x2, T* y) {
   if (!n) return;
@@ -202,8 +253,9 @@ template <class T> __global__ void k_sub_ratio(size_t n, const double* num, cons
   __shared__ double sk_v;
   if (threadIdx.x == 0) sk_v = scale * (*num) / (den ? *den : 1.0);
   __syncthreads();
-  SK_IDX;
-  x[i] -= (T)sk_v;
+  SK_LOOP(i) {
+    x[i] -= (T)sk_v;
+  }
 }
 template <class T> void sub_mean(const Exec& ex, size_t n, const double* sum, double count, T* r) {
   if (!n) return;
@@ -219,23 +271,28 @@ template <class T> void sub_ratio(const Exec& ex, size_t n, const double* num, c
 }
 
 template <class T>
-__global__ void k_cheb_first(size_t n, size_t rows, const T* __restrict__ dinv, const T* __restrict__ b, T c,
+__global__ void k_cheb_first(size_t n, const T* __restrict__ dinv, const T* __restrict__ b, T c,
                              T* __restrict__ d, T* __restrict__ x) {
-  SK_IDX;
-  T v = c * dinv[i % rows] * b[i];  // component-major: row of entry i is i mod rows
-  d[i] = v;
-  x[i] = v;
+  // component-major: blockIdx.y is the component, n the rows of one component
+  const size_t off = (size_t)blockIdx.y * n;
+  SK_LOOP(i) {
+    const T v = c * dinv[i] * b[off + i];
+    d[off + i] = v;
+    x[off + i] = v;
+  }
 }
 template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* dinv, const T* b, double c, T* d, T* x) {
   if (!n) return;
   ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * (n * 3 + n / nr));
-  k_cheb_first<T><<<SK_GRID(n)>>>(n, n / nr, dinv, b, (T)c, d, x);
+  const size_t rows = n / nr;
+  k_cheb_first<T><<<dim3(std::max(1, ew_grid(rows) / nr), nr), 256, 0, ex.s>>>(rows, dinv, b, (T)c, d, x);
   SK_CHECK_LAUNCH();
 }
 
 template <class S, class D> __global__ void k_convert(size_t n, const S* __restrict__ x, D* __restrict__ y) {
-  SK_IDX;
-  y[i] = (D)x[i];
+  SK_LOOP(i) {
+    y[i] = (D)x[i];
+  }
 }
 template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D* y) {
   if (!n) return;
@@ -244,8 +301,9 @@ template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D
   SK_CHECK_LAUNCH();
 }
 template <class S, class D> __global__ void k_add_convert(size_t n, const S* __restrict__ x, D* __restrict__ y) {
-  SK_IDX;
-  y[i] += (D)x[i];
+  SK_LOOP(i) {
+    y[i] += (D)x[i];
+  }
 }
 template <class S, class D> void add_convert(const Exec& ex, size_t n, const S* x, D* y) {
   if (!n) return;
@@ -269,7 +327,7 @@ __global__ void k_expand(int n, const double* __restrict__ ured, double* __restr
 void expand_velocity(const Exec& ex, int n, const double* ured, double* uall) {
   size_t tot = (size_t)(2 * n + 1) * (2 * n + 1) * (2 * n + 1);
   ProfScope ps(ex, STOKES_KERNEL_OTHER, 48.0 * tot);
-  k_expand<<<SK_GRID(tot)>>>(n, ured, uall);
+  k_expand<<<cdiv((long long)tot, 256), 256, 0, ex.s>>>(n, ured, uall);  // one thread per node
   SK_CHECK_LAUNCH();
 }
 __global__ void k_restrict_vel(int n, const double* __restrict__ uall, double* __restrict__ ured) {
@@ -284,13 +342,14 @@ __global__ void k_restrict_vel(int n, const double* __restrict__ uall, double* _
 void restrict_velocity(const Exec& ex, int n, const double* uall, double* ured) {
   size_t tot = (size_t)(2 * n - 1) * (2 * n - 1) * (2 * n - 1);
   ProfScope ps(ex, STOKES_KERNEL_OTHER, 48.0 * tot);
-  k_restrict_vel<<<SK_GRID(tot)>>>(n, uall, ured);
+  k_restrict_vel<<<cdiv((long long)tot, 256), 256, 0, ex.s>>>(n, uall, ured);
   SK_CHECK_LAUNCH();
 }
 
 __global__ void k_nonfinite(size_t n, const double* __restrict__ x, int* flag) {
-  SK_IDX;
-  if (!isfinite(x[i])) atomicOr(flag, 2);
+  SK_LOOP(i) {
+    if (!isfinite(x[i])) atomicOr(flag, 2);
+  }
 }
 __global__ void k_split_f64(size_t n, const double* __restrict__ x, float* __restrict__ hi,
                             float* __restrict__ lo) {

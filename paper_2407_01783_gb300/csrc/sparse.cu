@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
   if (inner) {
 #pragma unroll 4
     for (int e = 0; e < S; ++e) {
-      const T w = (T)vr[e * rc];
+      const T w = (T)__ldcs(&vr[e * rc]);  // streamed once: evict first
       const size_t cc = (size_t)(row + a.lin[db + e]);
 #pragma unroll
       for (int q = 0; q < NR; ++q) acc[q] += w * x[q * xs + cc];
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
     for (int e = 0; e < S; ++e) {
       const int de = db + e;
       const bool ok = st_inside(a, qx + a.d[de][0], qy + a.d[de][1], qz + a.d[de][2]);
-      const T w = ok ? (T)vr[e * rc] : T(0);
+      const T w = ok ? (T)__ldcs(&vr[e * rc]) : T(0);
       const size_t cc = (size_t)(ok ? row + a.lin[de] : row);
 #pragma unroll
       for (int q = 0; q < NR; ++q) acc[q] += w * x[q * xs + cc];
