@@ -259,6 +259,7 @@ def run_ours(args):
         for mu in mus:
             opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles,
                                             schur_inner_iters=args.schur_inner_iters, format=args.format,
+                                            vel_prec=args.vel_prec,
                                             **extra)
             S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
             f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
@@ -530,6 +531,8 @@ def main():
     ap.add_argument("--no-coupled96", action="store_true", help="skip the 96^3 coupled-vs-Schur comparison")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
+    ap.add_argument("--vel-prec", type=int, default=3, choices=[1, 2, 3],
+                    help="velocity preconditioner A~_1, A~_2 or A~_3 (default)")
     ap.add_argument("--format", type=int, default=0,
                     help="matrix storage: 0 stencil on large levels, 1 CSR, 2 stencil everywhere")
     ap.add_argument("--schur-inner-iters", type=int, default=2,

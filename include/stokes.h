@@ -104,6 +104,14 @@ typedef struct {
                             from a CUDA graph captured on the context's stream
                             at the second V-cycle (the first runs them eagerly);
                             0: plain launches */
+  int vel_prec;          /* velocity preconditioner inside A^{-1} solves and the
+                            block preconditioners (Sec. 5.1, Eqs.
+                            precond_A_plus_lambda_D_1..3): 3 (default) A~_3 =
+                            M_V/dt + mu L_V, one scalar V-cycle per component;
+                            2: A~_2 = A; 1: A~_1 = A + gamma mu D (D the
+                            grad-div matrix); 1 and 2 run a V-cycle on the 3x3
+                            block operator (re-assembled on every level,
+                            point-Jacobi Chebyshev smoothing) */
 } stokes_options;
 
 typedef struct {
@@ -186,10 +194,13 @@ typedef enum {
   STOKES_OP_PROLONG_P1 = 15,  /* y(level) = P x(level+1)                       */
   STOKES_OP_LOAD = 16,        /* y = M_V f on interior rows, x = nodal f on all
                                  nodes [(2n+1)^3][3] (node-interleaved)       */
-  STOKES_OP_A_DF = 17         /* y = A x as the mixed-precision refinement
+  STOKES_OP_A_DF = 17,        /* y = A x as the mixed-precision refinement
                                  residual computes it: FP32 hi/lo pairs of A
                                  and x, exact FP32 products, double-float sums
                                  (mixed-precision contexts only)              */
+  STOKES_OP_VCYCLE_VEL = 18   /* y = the configured velocity preconditioner
+                                 (vcycles V-cycles of A~_{vel_prec}) applied
+                                 to x, from level 0                          */
 } stokes_op;
 
 stokes_status stokes_apply(stokes_ctx* ctx, int op, int level, const double* x, double* y);
@@ -220,7 +231,9 @@ typedef enum {
   STOKES_MAT_BT = 3,   /* 3x1 blocks, interior P2 x P1                        */
   STOKES_MAT_MQ = 4, STOKES_MAT_LQ = 5,
   STOKES_MAT_KQ = 6,   /* any level */
-  STOKES_MAT_LUMPED = 7/* diagonal Lambda_V per interior P2 node (rows=cols) */
+  STOKES_MAT_LUMPED = 7,/* diagonal Lambda_V per interior P2 node (rows=cols) */
+  STOKES_MAT_AV = 8    /* BSR 3x3 velocity preconditioner A~_1 / A~_2 (any
+                          level; vel_prec 1 or 2 only)                       */
 } stokes_matrix;
 
 /* dims = {rows, cols, nnz (blocks), block_rows, block_cols}. */

@@ -23,8 +23,8 @@ PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 OP = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED_INV=7, VCYCLE_A3=8, VCYCLE_KQ=9,
           SCHUR_PREC=10, SCHUR=11, AGAMMA=12, PROLONG_P2=13, RESTRICT_P2=14, PROLONG_P1=15,
-          LOAD=16, A_DF=17)
-MAT = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED=7)
+          LOAD=16, A_DF=17, VCYCLE_VEL=18)
+MAT = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED=7, AV=8)
 KERNEL = dict(SPMM_A3=0, SPMV_A=1, B=2, BT=3, SPMV_P1=4, TRANSFER=5, BLAS1=6, OTHER=7,
               SPMM_A3_COARSE=8, RESIDUAL=9)
 
@@ -38,7 +38,7 @@ class StokesOptions(C.Structure):
         ("eps_pressure", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
         ("max_refine", C.c_int), ("profile", C.c_int), ("spmv_group", C.c_int),
         ("schur_inner_iters", C.c_int), ("pass_tol", C.c_double), ("format", C.c_int),
-        ("graphs", C.c_int),
+        ("graphs", C.c_int), ("vel_prec", C.c_int),
     ]
 
     def as_dict(self):

@@ -828,8 +828,41 @@ __global__ void k_diag_inv(int rows, const int* __restrict__ rp, const int* __re
   dinv[r] = pos >= 0 ? 1.0 / v[pos] : 0.0;
 }
 
+__global__ void k_diag_inv3(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ v, long long nnz, double* __restrict__ dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int pos = find_col(col, rp[i], rp[i + 1], i);
+  for (int r = 0; r < 3; ++r) {
+    const double a = pos >= 0 ? v[(size_t)(4 * r) * nnz + pos] : 0.0;  // plane 3r + r
+    dinv[(size_t)r * rows + i] = a != 0.0 ? 1.0 / a : 0.0;
+  }
+}
+
 void diag_inverse(const Exec& ex, const Csr& m, double* dinv) {
-  k_diag_inv<<<cdiv(m.rows, 256), 256, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, dinv);
+  if (m.br == 3) {
+    k_diag_inv3<<<cdiv(m.rows, 256), 256, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, m.nnz, dinv);
+  } else {
+    k_diag_inv<<<cdiv(m.rows, 256), 256, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, dinv);
+  }
+  SK_CHECK_LAUNCH();
+}
+
+// A~_1 = A + g mu D with mu D = A - A~_3 (x) I on interior velocities (E_V =
+// L_V + D on H^1_0): (1 + g) A - g A~_3 on the diagonal planes 0, 4, 8
+__global__ void k_combine_grad_div(long long nnz, const double* __restrict__ abs, const double* __restrict__ a3,
+                                   double g, double* __restrict__ out) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz;
+       k += (long long)gridDim.x * blockDim.x)
+    for (int j = 0; j < 9; ++j) {
+      const size_t i = (size_t)j * nnz + k;
+      out[i] = (1.0 + g) * abs[i] - ((j % 4) == 0 ? g * a3[k] : 0.0);
+    }
+}
+
+void combine_grad_div(const Exec& ex, long long nnz, const double* abs, const double* a3, double g, double* out) {
+  if (!nnz) return;
+  k_combine_grad_div<<<(int)std::min<long long>(cdiv(nnz, 256), 4096), 256, 0, ex.s>>>(nnz, abs, a3, g, out);
   SK_CHECK_LAUNCH();
 }
 

@@ -75,17 +75,24 @@ static void spd_inverse(std::vector<double>& A, int m) {
     }
 }
 
+// Dense inverse of a coarsest-level matrix; a BSR3 matrix is expanded over the
+// component-major unknowns (component r of node i at r * rows + i).
 static void coarse_inverse(stokes_ctx& c, const Csr& M, double** out64) {
-  int m = M.rows;
-  std::vector<int> rp(m + 1), col(M.nnz);
-  std::vector<double> v(M.nnz);
-  SK_CUDA(cudaMemcpyAsync(rp.data(), M.rowptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, c.ex.s));
+  const int rows = M.rows, bs = M.br;
+  const int m = rows * bs;
+  const size_t planes = (size_t)bs * bs;
+  std::vector<int> rp(rows + 1), col(M.nnz);
+  std::vector<double> v(planes * M.nnz);
+  SK_CUDA(cudaMemcpyAsync(rp.data(), M.rowptr, sizeof(int) * (rows + 1), cudaMemcpyDeviceToHost, c.ex.s));
   SK_CUDA(cudaMemcpyAsync(col.data(), M.col, sizeof(int) * M.nnz, cudaMemcpyDeviceToHost, c.ex.s));
-  SK_CUDA(cudaMemcpyAsync(v.data(), M.v64, sizeof(double) * M.nnz, cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaMemcpyAsync(v.data(), M.v64, sizeof(double) * planes * M.nnz, cudaMemcpyDeviceToHost, c.ex.s));
   SK_CUDA(cudaStreamSynchronize(c.ex.s));
   std::vector<double> A((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i)
-    for (int k = rp[i]; k < rp[i + 1]; ++k) A[(size_t)i * m + col[k]] = v[k];
+  for (int i = 0; i < rows; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      for (int r = 0; r < bs; ++r)
+        for (int q = 0; q < bs; ++q)
+          A[(size_t)(r * rows + i) * m + (q * rows + col[k])] = v[(size_t)(r * bs + q) * M.nnz + k];
   spd_inverse(A, m);
   *out64 = c.arena.alloc<double>((size_t)m * m);
   SK_CUDA(cudaMemcpy(*out64, A.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice));
@@ -140,13 +147,15 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     Csr p2, p1, b, bt;
     build_pattern(c.ex, c.arena, st, PAT_P2P2, L.n, p2);
     build_pattern(c.ex, c.arena, st, PAT_P1P1, L.n, p1);
+    const bool block_mg = c.opt.vel_prec != 3;
     AssemblyOut o;
     o.a3 = c.arena.alloc<double>(p2.nnz);
     o.kq = c.arena.alloc<double>(p1.nnz);
+    if (block_mg) o.abs = c.arena.alloc<double>(9 * (size_t)p2.nnz);
     if (l == 0) {
       build_pattern(c.ex, c.arena, st, PAT_P1P2, L.n, b);
       build_pattern(c.ex, c.arena, st, PAT_P2P1, L.n, bt);
-      o.abs = c.arena.alloc<double>(9 * (size_t)p2.nnz);
+      if (!o.abs) o.abs = c.arena.alloc<double>(9 * (size_t)p2.nnz);
       o.mq = c.arena.alloc<double>(p1.nnz);
       o.lq = c.arena.alloc<double>(p1.nnz);
       o.b = c.arena.alloc<double>(3 * (size_t)b.nnz);
@@ -165,6 +174,18 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     L.KQ_dinv64 = c.arena.alloc<double>(L.KQ.rows);
     diag_inverse(c.ex, L.A3, L.A3_dinv64);
     diag_inverse(c.ex, L.KQ, L.KQ_dinv64);
+    if (block_mg) {
+      L.AV = p2;
+      L.AV.br = L.AV.bc = 3;
+      if (c.opt.vel_prec == 2) {
+        L.AV.v64 = o.abs;  // A~_2 = A
+      } else {
+        L.AV.v64 = c.arena.alloc<double>(9 * (size_t)p2.nnz);
+        combine_grad_div(c.ex, p2.nnz, o.abs, o.a3, c.gamma, L.AV.v64);
+      }
+      L.AV_dinv64 = c.arena.alloc<double>(3 * (size_t)L.AV.rows);
+      diag_inverse(c.ex, L.AV, L.AV_dinv64);
+    }
     if (l == 0) {
       c.A = p2;
       c.A.br = c.A.bc = 3;
@@ -204,9 +225,11 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   Level& Lc = c.lv.back();
   coarse_inverse(c, Lc.A3, &Lc.A3_cinv64);
   coarse_inverse(c, Lc.KQ, &Lc.KQ_cinv64);
+  if (Lc.AV.v64) coarse_inverse(c, Lc.AV, &Lc.AV_cinv64);
   for (size_t l = 0; l + 1 < c.lv.size(); ++l) {
     c.lv[l].A3_lmax = estimate_lmax(c, c.lv[l].A3, c.lv[l].A3_dinv64, 15, 1000 + l);
     c.lv[l].KQ_lmax = estimate_lmax(c, c.lv[l].KQ, c.lv[l].KQ_dinv64, 15, 2000 + l);
+    if (c.lv[l].AV.v64) c.lv[l].AV_lmax = estimate_lmax(c, c.lv[l].AV, c.lv[l].AV_dinv64, 15, 3000 + l);
   }
   // fine-level auxiliaries
   const Level& L0 = c.lv[0];
@@ -248,12 +271,17 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
       L.KQ.v32 = f32_copy(c, L.KQ.v64, L.KQ.nnz);
       L.A3_dinv32 = f32_copy(c, L.A3_dinv64, L.A3.rows);
       L.KQ_dinv32 = f32_copy(c, L.KQ_dinv64, L.KQ.rows);
+      if (L.AV.v64) {
+        L.AV.v32 = L.AV.v64 == c.A.v64 ? c.A.v32 : f32_copy(c, L.AV.v64, 9 * (size_t)L.AV.nnz);
+        L.AV_dinv32 = f32_copy(c, L.AV_dinv64, 3 * (size_t)L.AV.rows);
+      }
       for (Csr* t : {&L.P2, &L.R2, &L.P1, &L.R1})
         if (t->v64) t->v32 = f32_copy(c, t->v64, t->nnz);
     }
     for (auto& so : c.stencils) so->v32 = f32_copy(c, so->v64, so->total);
     Lc.A3_cinv32 = f32_copy(c, Lc.A3_cinv64, (size_t)Lc.A3.rows * Lc.A3.rows);
     Lc.KQ_cinv32 = f32_copy(c, Lc.KQ_cinv64, (size_t)Lc.KQ.rows * Lc.KQ.rows);
+    if (Lc.AV_cinv64) Lc.AV_cinv32 = f32_copy(c, Lc.AV_cinv64, 9 * (size_t)Lc.AV.rows * Lc.AV.rows);
   }
   // threads-per-row: tuned in the precision of the hot loop unless fixed by the caller
   auto tune = [&](Csr& m, int nr, int kind) {
@@ -276,6 +304,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   for (Level& L : c.lv) {
     tune(L.A3, 3, 0);
     tune(L.KQ, 1, 0);
+    if (L.AV.v64) tune(L.AV, 3, 1);
     if (L.P2.rows) {
       tune(L.P2, 3, 0);
       tune(L.R2, 3, 0);
@@ -333,6 +362,7 @@ void stokes_default_options(stokes_options* o) {
   o->pass_tol = 3e-2;
   o->format = 0;
   o->graphs = 1;
+  o->vel_prec = 3;
 }
 
 const char* stokes_status_string(int s) {
@@ -367,7 +397,7 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
   if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
   if (c->opt.vcycles < 1 || c->opt.cheb_degree < 1 || c->opt.restart < 2 || !(c->opt.eps_pressure > 0) ||
       !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 2 ||
-      !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1)) {
+      !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1) || c->opt.vel_prec < 1 || c->opt.vel_prec > 3) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;
@@ -485,6 +515,7 @@ static const Csr* matrix_of(stokes_ctx* c, int which, int level) {
     case STOKES_MAT_MQ: return level == 0 ? &c->MQ : nullptr;
     case STOKES_MAT_LQ: return level == 0 ? &c->LQ : nullptr;
     case STOKES_MAT_KQ: return &c->lv[level].KQ;
+    case STOKES_MAT_AV: return c->lv[level].AV.v64 ? &c->lv[level].AV : nullptr;
     default: return nullptr;
   }
 }

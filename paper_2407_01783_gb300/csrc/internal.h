@@ -246,6 +246,15 @@ struct Level {
   // coarsest level: dense inverses (row-major)
   double *A3_cinv64 = nullptr, *KQ_cinv64 = nullptr;
   float *A3_cinv32 = nullptr, *KQ_cinv32 = nullptr;
+  // 3x3-block velocity preconditioner A~_1 or A~_2 (vel_prec 1, 2): BSR3 on
+  // the P2 pattern, point-Jacobi diagonal [3][rows], dense inverse on the
+  // coarsest level over the component-major (3 rows) unknowns
+  Csr AV;
+  double* AV_dinv64 = nullptr;
+  float* AV_dinv32 = nullptr;
+  double AV_lmax = 0;
+  double* AV_cinv64 = nullptr;
+  float* AV_cinv32 = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -277,7 +286,10 @@ void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat,
 void assemble_load_transpose(const Exec& ex, int n, const double* X, const double* lu, double* out);
 void build_transfer_p2(const Exec& ex, Arena& ar, int nf, int nc, Csr& P, Csr& R);
 void build_transfer_p1(const Exec& ex, Arena& ar, int nf, int nc, Csr& P, Csr& R);
+// scalar CSR: dinv[i] = 1 / m_ii; BSR3: dinv[r * rows + i] = 1 / (m_ii)_rr
 void diag_inverse(const Exec& ex, const Csr& m, double* dinv);
+// out = (1 + g) a_bsr3 - g (a3 on the diagonal of every 3x3 block), same pattern
+void combine_grad_div(const Exec& ex, long long nnz, const double* abs, const double* a3, double g, double* out);
 // Stencil storage of a square P2-interior (p2 = 1) or P1 (p2 = 0) matrix of
 // level size n, values copied from the assembled CSR m (FP64; FP32 on request).
 StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int p2, int n, const Csr& m);
@@ -312,6 +324,9 @@ template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y,
 // only (FP64 throughput is a small fraction of FP32 on this GPU).
 void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y,
                       int kind);
+// Chebyshev step on a BSR3 operator with a per-component diagonal dinv[3][rows]
+template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
+                                  const T* dinv, double c1, double c2, int kind);
 template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y);
 void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
 
@@ -395,8 +410,9 @@ struct stokes_ctx {
   // host staging for *_host calls
   double *f_dev = nullptr, *g_dev = nullptr, *u_dev = nullptr, *p_dev = nullptr;
   cudaEvent_t ev_read = nullptr;  // host reads of device scalars
-  // levels >= 1 of the V-cycle of A~_3 (which = 0) and of eps M_Q + L_Q
-  // (which = 1), FP64 [0] and FP32 [1]: fixed input/output vectors, a private
+  // levels >= 1 of the V-cycle of A~_3 (which = 0), of eps M_Q + L_Q
+  // (which = 1) and of the block operator A~_1 / A~_2 (which = 2), FP64 [0]
+  // and FP32 [1]: fixed input/output vectors, a private
   // vector pool for the temporaries, and the captured graph
   struct CoarseGraph {
     int state = 0;  // 0: next call runs eagerly, 1: next call captures, 2: replay
@@ -405,7 +421,7 @@ struct stokes_ctx {
     sk::VecPool pool;
     cudaGraphExec_t exec = nullptr;
     sk::Prof::Counts counts;
-  } cgraph[2][2];
+  } cgraph[3][2];
   // graphs are captured on this private stream (capture is not allowed on the
   // legacy default stream) and launched on ex.s
   cudaStream_t cap_stream = nullptr;
@@ -422,6 +438,8 @@ int adjoint_context(stokes_ctx* c, const double* dJdu, const double* dJdp, doubl
                     double* dJdf, double* dJdg, double* dJdmu, stokes_info* info);
 void apply_operator(stokes_ctx* c, int op, int level, const double* x, double* y);
 double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps, uint64_t seed);
+// velocity V-cycle kind: 0 (scalar A~_3 per component) or 2 (block A~_1 / A~_2)
+inline int velocity_cycle(const stokes_ctx& c) { return c.opt.vel_prec == 3 ? 0 : 2; }
 void set_last_error(const std::string& msg);  // message returned by stokes_last_error()
 void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
 }  // namespace sk

@@ -75,20 +75,26 @@ static size_t npres(const stokes_ctx& c) { return (size_t)c.lv[0].np; }
 template <class T>
 static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double lmin, double lmax, int steps,
                      const T* b, T* x, bool xzero, int kind) {
-  size_t len = (size_t)M.rows * nr;
+  // a 3x3-block operator (M.br == 3) has one diagonal entry per component
+  const bool block = M.br == 3;
+  size_t len = (size_t)M.rows * (block ? 3 : nr);
   double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta, rho = 1.0 / sigma;
   Tmp<T> d(c.pool, len), xt(c.pool, len);
   T* xa = x;
   T* xb = xt;
+  auto step = [&](const T* xin, T* xout, double c1, double c2) {
+    if (block) bsr3_cheb<T>(c.ex, M, b, xin, d, xout, dinv, c1, c2, kind);
+    else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind);
+  };
   if (xzero) {
-    cheb_first<T>(c.ex, len, nr, dinv, b, 1.0 / theta, d, xa);
+    cheb_first<T>(c.ex, len, block ? 1 : nr, dinv, b, 1.0 / theta, d, xa);
   } else {
-    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, 0.0, 1.0 / theta, kind);
+    step(xa, xb, 0.0, 1.0 / theta);
     std::swap(xa, xb);
   }
   for (int k = 1; k < steps; ++k) {
     double rn = 1.0 / (2.0 * sigma - rho);
-    spmv_cheb<T>(c.ex, M, nr, b, xa, d, xb, dinv, rn * rho, 2.0 * rn / delta, kind);
+    step(xa, xb, rn * rho, 2.0 * rn / delta);
     std::swap(xa, xb);
     rho = rn;
   }
@@ -118,7 +124,7 @@ static bool coarse_graph_ok(const stokes_ctx& c, int which) {
   const auto& G = c.cgraph[which][0].state == 2 ? c.cgraph[which][0] : c.cgraph[which][1];
   if (G.state == 2) return G.counts.launches[k] == 0;
   return !(k == STOKES_KERNEL_TRANSFER || k == STOKES_KERNEL_BLAS1 || k == STOKES_KERNEL_OTHER ||
-           k == (which ? STOKES_KERNEL_SPMV_P1 : STOKES_KERNEL_SPMM_A3_COARSE));
+           k == (which == 1 ? STOKES_KERNEL_SPMV_P1 : STOKES_KERNEL_SPMM_A3_COARSE));
 }
 
 // swaps the context's vector pool with a graph's private one for a scope
@@ -170,23 +176,39 @@ template <class T> static void coarse_run(stokes_ctx& c, int which, stokes_ctx::
     }
 }
 
+// level operator of V-cycle kind `which`
+static const Csr& level_op(const Level& L, int which) { return which == 1 ? L.KQ : (which == 2 ? L.AV : L.A3); }
+
+// residual r = b - M x of a level operator (scalar with nr components or 3x3 blocks)
+template <class T>
+static void level_resid(stokes_ctx& c, const Csr& M, int nr, const T* b, const T* x, T* r, int kind) {
+  if (M.br == 3) bsr3_apply<T>(c.ex, M, x, r, b, kind);
+  else spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
+}
+
 template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero) {
   Level& L = c.lv[l];
-  const int nr = which ? 1 : 3;
-  const Csr& M = which ? L.KQ : L.A3;
+  const int nr = which == 1 ? 1 : 3;
+  const Csr& M = level_op(L, which);
   size_t len = (size_t)M.rows * nr;
   if (l + 1 == (int)c.lv.size()) {
+    if (which == 2) {  // dense inverse over all 3 rows components
+      dense_apply<T>(c.ex, pick<T>(L.AV_cinv64, L.AV_cinv32), 3 * M.rows, 1, b, x);
+      return;
+    }
     const T* Minv = which ? pick<T>(L.KQ_cinv64, L.KQ_cinv32) : pick<T>(L.A3_cinv64, L.A3_cinv32);
     dense_apply<T>(c.ex, Minv, M.rows, nr, b, x);
     return;
   }
-  const T* dinv = which ? pick<T>(L.KQ_dinv64, L.KQ_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32);
-  double lmax = kChebHigh * (which ? L.KQ_lmax : L.A3_lmax), lmin = kChebLow * (which ? L.KQ_lmax : L.A3_lmax);
+  const T* dinv = which == 1 ? pick<T>(L.KQ_dinv64, L.KQ_dinv32)
+                             : (which == 2 ? pick<T>(L.AV_dinv64, L.AV_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32));
+  const double lhat = which == 1 ? L.KQ_lmax : (which == 2 ? L.AV_lmax : L.A3_lmax);
+  double lmax = kChebHigh * lhat, lmin = kChebLow * lhat;
   int deg = std::max(1, c.opt.cheb_degree);
-  const int kind = which ? STOKES_KERNEL_SPMV_P1 : (l == 0 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMM_A3_COARSE);
+  const int kind = which == 1 ? STOKES_KERNEL_SPMV_P1 : (l == 0 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMM_A3_COARSE);
   cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind);
   Level& Lc = c.lv[l + 1];
-  const Csr& Mc = which ? Lc.KQ : Lc.A3;
+  const Csr& Mc = level_op(Lc, which);
   size_t lenc = (size_t)Mc.rows * nr;
   if (l == 0 && coarse_graph_ok(c, which)) {
     auto& G = c.cgraph[which][std::is_same<T, float>::value ? 1 : 0];
@@ -197,18 +219,18 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
     }
     {
       Tmp<T> r(c.pool, len);
-      spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
-      spmv_store<T>(c.ex, which ? L.R1 : L.R2, nr, r, (T*)G.b, STOKES_KERNEL_TRANSFER);
+      level_resid<T>(c, M, nr, b, x, r, kind);
+      spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, (T*)G.b, STOKES_KERNEL_TRANSFER);
     }
     coarse_run<T>(c, which, G);
-    spmv_add<T>(c.ex, which ? L.P1 : L.P2, nr, (const T*)G.x, x, STOKES_KERNEL_TRANSFER);
+    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, (const T*)G.x, x, STOKES_KERNEL_TRANSFER);
   } else {
     Tmp<T> r(c.pool, len);
-    spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
+    level_resid<T>(c, M, nr, b, x, r, kind);
     Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);
-    spmv_store<T>(c.ex, which ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER);
+    spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER);
     vcycle<T>(c, which, l + 1, bc, xc, true);
-    spmv_add<T>(c.ex, which ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER);
+    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER);
   }
   cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind);
 }
@@ -303,7 +325,8 @@ template <class T> static int ainv(stokes_ctx& c, const T* t, T* w, double tol) 
   bool ok = true;
   int it = pcg<T>(
       c, nvel(c), [&](const T* x, T* y) { op_A<T>(c, x, y); },
-      [&](const T* r, T* z) { vcycles<T>(c, 0, r, z, std::max(1, c.opt.vcycles)); }, t, w, tol, c.opt.max_inner, &ok);
+      [&](const T* r, T* z) { vcycles<T>(c, velocity_cycle(c), r, z, std::max(1, c.opt.vcycles)); }, t, w, tol,
+      c.opt.max_inner, &ok);
   c.inner_iters += it;
   if (!ok) c.inner_capped = true;
   return it;
@@ -438,7 +461,7 @@ template <class T> static void atilde_inv(stokes_ctx& c, const T* r, T* z, doubl
   if (c.opt.m2_inner_cg)
     ainv<T>(c, r, z, tol_in);
   else
-    vcycles<T>(c, 0, r, z, std::max(1, c.opt.vcycles));
+    vcycles<T>(c, velocity_cycle(c), r, z, std::max(1, c.opt.vcycles));
 }
 
 template <class T> static void block_prec(stokes_ctx& c, const T* ru, const T* rp, T* zu, T* zp, double tol_in) {
@@ -820,6 +843,10 @@ void apply_operator(stokes_ctx* cp, int op, int level, const double* x, double* 
       break;
     }
     case STOKES_OP_VCYCLE_KQ: vcycles<double>(c, 1, x, y, 1); break;
+    case STOKES_OP_VCYCLE_VEL:
+      SK_REQUIRE(level == 0, STOKES_ERR_ARG, "V-cycle from level 0 only");
+      vcycles<double>(c, velocity_cycle(c), x, y, std::max(1, c.opt.vcycles));
+      break;
     case STOKES_OP_SCHUR_PREC: cprec<double>(c, x, y); break;
     case STOKES_OP_SCHUR: {
       Tmp<double> t(c.pool, nv), w(c.pool, nv);
@@ -865,7 +892,7 @@ void apply_operator(stokes_ctx* cp, int op, int level, const double* x, double* 
 // lambda_max(D^{-1} M) from the Lanczos tridiagonal of `steps` Jacobi-PCG
 // steps (the CG coefficients give the Lanczos matrix; Golub & Van Loan 10.2).
 double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps, uint64_t seed) {
-  const size_t n = M.rows;
+  const size_t n = (size_t)M.rows * M.br;  // 3x3 blocks: all components, component-major
   if (n == 0) return 1.0;
   std::vector<double> hb(n);
   uint64_t st = seed * 0x9E3779B97F4A7C15ULL + 1;
@@ -887,7 +914,8 @@ double estimate_lmax(stokes_ctx& c, const Csr& M, const double* dinv, int steps,
   double rz = read_now(c, D, s);
   std::vector<double> al, be;
   for (int j = 0; j < steps; ++j) {
-    spmv_store<double>(c.ex, M, 1, d, q, -1);
+    if (M.br == 3) bsr3_apply<double>(c.ex, M, d, q, nullptr, -1);
+    else spmv_store<double>(c.ex, M, 1, d, q, -1);
     dot1<double>(c, (const double*)d, (const double*)q, n, D + 1);
     double dq = read_now(c, D + 1, s + 1);
     if (!(dq > 0) || !(rz > 0)) break;

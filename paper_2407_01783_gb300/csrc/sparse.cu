@@ -143,6 +143,27 @@ template <class T, int NR> struct EpiCheb {
   }
 };
 
+// Same step with a diagonal per component (3x3-block operators): dinv[r*ns+row]
+template <class T> struct EpiCheb3 {
+  const T* b;
+  const T* xin;
+  T* d;
+  T* xout;
+  const T* dinv;
+  T c1, c2;
+  size_t ns;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      size_t i = r * ns + row;
+      T res = b[i] - acc[r];
+      T dn = c1 * d[i] + c2 * dinv[i] * res;
+      d[i] = dn;
+      xout[i] = xin[i] + dn;
+    }
+  }
+};
+
 template <int G, class T, int NR>
 __device__ __forceinline__ void group_reduce(T* acc) {
 #pragma unroll
@@ -599,6 +620,12 @@ template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T*
   if (nr == 3) launch(ex, m, SH_CSR3, xin, EpiCheb<T, 3>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
   else launch(ex, m, SH_CSR1, xin, EpiCheb<T, 1>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
 }
+template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
+                                  const T* dinv, double c1, double c2, int kind) {
+  // streams as in the scalar step, over 3 components and a 3-component diagonal
+  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), 3, 3, 4) + 3.0 * sizeof(T) * m.rows);
+  launch(ex, m, SH_BSR3, xin, EpiCheb3<T>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
+}
 template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, int kind) {
   ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), 3, 3, b ? 1 : 0));
   if (b) launch(ex, m, SH_BSR3, x, EpiResid<T, 3>{b, y, (size_t)m.rows}, m.group);
@@ -771,6 +798,7 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
                              double, int);                                                                     \
   template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, int);                          \
+  template void bsr3_cheb<T>(const Exec&, const Csr&, const T*, const T*, T*, T*, const T*, double, double, int); \
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double);                     \
   template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double);          \
   template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*);

@@ -146,3 +146,17 @@ def test_error_statuses():
     with pytest.raises(sk.StokesError) as e:
         sk.Stokes(4, V, -1.0, 0.01)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("vel_prec,gamma,method", [(2, 0.0, 0), (1, 1.0, 0), (2, 0.0, 1), (1, 10.0, 1)])
+def test_block_velocity_preconditioners_match_oracle(vel_prec, gamma, method):
+    """A~_2 and A~_1 (3x3-block V-cycles) inside the A^{-1} solves of Method 1
+    and the block preconditioner of Method 2 give the same discrete solution."""
+    r = run_case(6, 1e-2, 1e-3, 0.2, 13, gamma=gamma, g_seed=14, vel_prec=vel_prec, method=method)
+    assert r["eu"] <= PARITY and r["ep"] <= PARITY, r
+
+
+@pytest.mark.parametrize("vel_prec", [1, 2])
+def test_block_velocity_preconditioners_mixed(vel_prec):
+    r = run_case(8, 1e-2, 1e-3, 0.2, 2, gamma=1.0, tol=1e-8, precision=1, vel_prec=vel_prec)
+    assert r["info"]["status"] == 0 and r["res"] <= 1.5e-8, r
