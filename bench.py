@@ -50,14 +50,17 @@ def workload_name(n):
 
 
 INNER_ITERS = 2
+SCHUR_PREC, VEL_PREC = 0, 3
+SCHUR_NAME = {0: "C^Lambda", 1: "C^Delta", 2: "C_lambda (B M_V^-1 B^T, 8 Chebyshev steps)"}
+VEL_NAME = {3: "A~_3", 2: "A~_2 = A (3x3 blocks)", 1: "A~_1 = A + gamma mu D (3x3 blocks)"}
 
 
 def config(n, precision):
     return {"workload": workload_name(n), "n_cubes": n, "mus": list(MUS), "dt": DT,
             "jitter": JITTER, "seed": SEED, "tol": TOL, "precision": precision,
             "dofs_per_solve": 3 * (2 * n + 1) ** 3 + (n + 1) ** 3,
-            "solves_per_step": len(MUS), "method": "schur-cg", "schur_prec": "C^Lambda",
-            "velocity_prec": "A~_3, 1 V-cycle (Chebyshev-Jacobi degree 2)",
+            "solves_per_step": len(MUS), "method": "schur-cg", "schur_prec": SCHUR_NAME[SCHUR_PREC],
+            "velocity_prec": VEL_NAME[VEL_PREC] + ", 1 V-cycle (Chebyshev-Jacobi degree 2)",
             "schur_inner": ("fixed %d PCG iterations on B Lambda^-1 B^T (1 V-cycle of M_Q + L_Q)" % INNER_ITERS
                             if INNER_ITERS > 0 else "PCG on B Lambda^-1 B^T to rel. 1e-1"),
             "coarse_levels": "replayed from captured CUDA graphs",
@@ -259,7 +262,7 @@ def run_ours(args):
         for mu in mus:
             opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles,
                                             schur_inner_iters=args.schur_inner_iters, format=args.format,
-                                            vel_prec=args.vel_prec,
+                                            vel_prec=args.vel_prec, schur_prec=args.schur_prec,
                                             **extra)
             S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
             f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
@@ -531,6 +534,8 @@ def main():
     ap.add_argument("--no-coupled96", action="store_true", help="skip the 96^3 coupled-vs-Schur comparison")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
+    ap.add_argument("--schur-prec", type=int, default=0, choices=[0, 1, 2],
+                    help="Schur preconditioner C^Lambda (default), C^Delta or C_lambda (M_V)")
     ap.add_argument("--vel-prec", type=int, default=3, choices=[1, 2, 3],
                     help="velocity preconditioner A~_1, A~_2 or A~_3 (default)")
     ap.add_argument("--format", type=int, default=0,
@@ -544,8 +549,9 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
-    global INNER_ITERS
+    global INNER_ITERS, SCHUR_PREC, VEL_PREC
     INNER_ITERS = args.schur_inner_iters
+    SCHUR_PREC, VEL_PREC = args.schur_prec, args.vel_prec
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)

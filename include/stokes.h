@@ -61,9 +61,11 @@ typedef enum {
 } stokes_status;
 
 enum { STOKES_METHOD_SCHUR = 0, STOKES_METHOD_COUPLED = 1 };
-/* Schur-complement preconditioner: C^Lambda (lumped velocity mass, the
- * paper's recommendation) or C^Delta (pressure Laplacian). */
-enum { STOKES_SCHUR_PREC_LUMPED = 0, STOKES_SCHUR_PREC_LAPLACE = 1 };
+/* Schur-complement preconditioner (Eq. Schur_complement_preconditioners):
+ * C^Lambda (lumped velocity mass, the paper's recommendation), C^Delta
+ * (pressure Laplacian) or C_lambda (B M_V^{-1} B^T, with M_V^{-1} by
+ * mass_steps_v Chebyshev-Jacobi steps on the P2 mass). */
+enum { STOKES_SCHUR_PREC_LUMPED = 0, STOKES_SCHUR_PREC_LAPLACE = 1, STOKES_SCHUR_PREC_MASS = 2 };
 /* FP64 everywhere, or FP32 matrices/multigrid/inner Krylov with FP64 outer
  * refinement, dot products, pressure-mean projection and coarse factors. */
 enum { STOKES_PRECISION_FP64 = 0, STOKES_PRECISION_MIXED = 1 };
@@ -112,6 +114,10 @@ typedef struct {
                             grad-div matrix); 1 and 2 run a V-cycle on the 3x3
                             block operator (re-assembled on every level,
                             point-Jacobi Chebyshev smoothing) */
+  int mass_steps_v;      /* Chebyshev-Jacobi steps for (M_V)^{-1} inside C_lambda
+                            (schur_prec = STOKES_SCHUR_PREC_MASS) on the exact
+                            P2 interval [1/4, 4.3475]: 8 (default, the paper's
+                            economical "2Vc" reading) ... 48 (~1e-10, "th") */
 } stokes_options;
 
 typedef struct {

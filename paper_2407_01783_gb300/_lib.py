@@ -18,7 +18,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NOT_CO
           -9: "ERR_MESH"}
 
 METHOD_SCHUR, METHOD_COUPLED = 0, 1
-SCHUR_PREC_LUMPED, SCHUR_PREC_LAPLACE = 0, 1
+SCHUR_PREC_LUMPED, SCHUR_PREC_LAPLACE, SCHUR_PREC_MASS = 0, 1, 2
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 OP = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED_INV=7, VCYCLE_A3=8, VCYCLE_KQ=9,
@@ -38,7 +38,7 @@ class StokesOptions(C.Structure):
         ("eps_pressure", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
         ("max_refine", C.c_int), ("profile", C.c_int), ("spmv_group", C.c_int),
         ("schur_inner_iters", C.c_int), ("pass_tol", C.c_double), ("format", C.c_int),
-        ("graphs", C.c_int), ("vel_prec", C.c_int),
+        ("graphs", C.c_int), ("vel_prec", C.c_int), ("mass_steps_v", C.c_int),
     ]
 
     def as_dict(self):

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
       int row = ri[ra];
       if (row < 0) continue;
       if (a.o.lumped) a.o.lumped[row] += tg.vol * (ra < 4 ? 3.0 / 32.0 : 1.0 / 5.0);
-      if (a.o.a3 || a.o.abs) {
+      if (a.o.a3 || a.o.abs || a.o.mv) {
         int lo = a.p2rp[row], hi = a.p2rp[row + 1];
         for (int cb = 0; cb < 10; ++cb) {
           int colj = ri[cb];
@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
             continue;
           }
           if (a.o.a3) a.o.a3[pos] += diag;
+          if (a.o.mv) a.o.mv[pos] += mass;
           if (a.o.abs) {
             // 2 eps(phi_a e_c):eps(phi_b e_d) = delta_cd grad.grad + d_d phi_a d_c phi_b
             for (int c = 0; c < 3; ++c)
@@ -478,6 +479,7 @@ long long assemble(const Exec& ex, int n, const double* X, double mu, double dt,
     if (p) SK_CUDA(cudaMemsetAsync(p, 0, cnt * sizeof(double), ex.s));
   };
   zero(out.a3, p2.nnz);
+  zero(out.mv, p2.nnz);
   zero(out.abs, 9 * (size_t)p2.nnz);
   zero(out.mq, p1.nnz);
   zero(out.lq, p1.nnz);

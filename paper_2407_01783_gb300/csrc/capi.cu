@@ -161,6 +161,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
       o.b = c.arena.alloc<double>(3 * (size_t)b.nnz);
       o.bt = c.arena.alloc<double>(3 * (size_t)bt.nnz);
       o.lumped = c.arena.alloc<double>(L.nvi);
+      if (c.opt.schur_prec == STOKES_SCHUR_PREC_MASS) o.mv = c.arena.alloc<double>(p2.nnz);
     }
     long long bad = assemble(c.ex, L.n, L.X, c.mu, c.dt, c.opt.eps_pressure, p2, p1, l == 0 ? &b : nullptr,
                              l == 0 ? &bt : nullptr, o, c.d_flag);
@@ -203,6 +204,12 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
       c.Bt.bc = 1;
       c.Bt.v64 = o.bt;
       c.lumped = o.lumped;
+      if (o.mv) {
+        c.MV = p2;
+        c.MV.v64 = o.mv;
+        c.MV_dinv64 = c.arena.alloc<double>(c.MV.rows);
+        diag_inverse(c.ex, c.MV, c.MV_dinv64);
+      }
     }
   }
   for (size_t l = 0; l + 1 < c.lv.size(); ++l) {
@@ -221,6 +228,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     }
     add(c.MQ, 0, n);
     add(c.LQ, 0, n);
+    if (c.MV.v64) add(c.MV, 1, n);
   }
   Level& Lc = c.lv.back();
   coarse_inverse(c, Lc.A3, &Lc.A3_cinv64);
@@ -266,6 +274,10 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     c.LQ.v32 = f32_copy(c, c.LQ.v64, c.LQ.nnz);
     c.lumped_inv32 = f32_copy(c, c.lumped_inv64, L0.nvi);
     c.MQ_dinv32 = f32_copy(c, c.MQ_dinv64, L0.np);
+    if (c.MV.v64) {
+      c.MV.v32 = f32_copy(c, c.MV.v64, c.MV.nnz);
+      c.MV_dinv32 = f32_copy(c, c.MV_dinv64, c.MV.rows);
+    }
     for (Level& L : c.lv) {
       L.A3.v32 = f32_copy(c, L.A3.v64, L.A3.nnz);
       L.KQ.v32 = f32_copy(c, L.KQ.v64, L.KQ.nnz);
@@ -300,6 +312,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   tune(c.B, 1, 2);
   tune(c.Bt, 3, 3);
   tune(c.MQ, 1, 0);
+  if (c.MV.v64) tune(c.MV, 3, 0);
   c.LQ.group = c.MQ.group;
   for (Level& L : c.lv) {
     tune(L.A3, 3, 0);
@@ -363,6 +376,7 @@ void stokes_default_options(stokes_options* o) {
   o->format = 0;
   o->graphs = 1;
   o->vel_prec = 3;
+  o->mass_steps_v = 8;
 }
 
 const char* stokes_status_string(int s) {
@@ -397,7 +411,8 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
   if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
   if (c->opt.vcycles < 1 || c->opt.cheb_degree < 1 || c->opt.restart < 2 || !(c->opt.eps_pressure > 0) ||
       !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 2 ||
-      !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1) || c->opt.vel_prec < 1 || c->opt.vel_prec > 3) {
+      !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1) || c->opt.vel_prec < 1 || c->opt.vel_prec > 3 ||
+      c->opt.schur_prec < 0 || c->opt.schur_prec > 2 || c->opt.mass_steps_v < 1) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;

@@ -275,6 +275,7 @@ struct AssemblyOut {
   double* b = nullptr;      // B (3 planes) on the P1P2 pattern
   double* bt = nullptr;     // B^T (3 planes) on the P2P1 pattern
   double* lumped = nullptr; // Lambda_V per interior node
+  double* mv = nullptr;     // scalar P2 mass M on the P2P2 pattern
 };
 // Returns the number of inverted/degenerate tetrahedra.
 long long assemble(const Exec& ex, int n, const double* X, double mu, double dt,
@@ -395,6 +396,9 @@ struct stokes_ctx {
   std::vector<sk::Level> lv;
   sk::Csr A, B, Bt, MQ, LQ;  // fine level (P2P2 BSR3, P1P2, P2P1, P1P1, P1P1)
   double* lumped = nullptr;  // Lambda_V per interior node
+  sk::Csr MV;                // scalar P2 mass (C_lambda only); M_V = MV per component
+  double* MV_dinv64 = nullptr;
+  float* MV_dinv32 = nullptr;
   double *lumped_inv64 = nullptr;
   float* lumped_inv32 = nullptr;
   double* MQ_dinv64 = nullptr;

@@ -23,6 +23,12 @@ constexpr double kChebHigh = 1.1;
 // D_K^{-1} M_K = (I + 1 1^T)/2 has eigenvalues 1/2 and 5/2; Wathen 1987).
 constexpr double kMassLow = 0.5;
 constexpr double kMassHigh = 2.5;
+// sigma(D^{-1} M) for the P2 velocity mass: the element pencil (M_K, diag M_K)
+// is the same for every affine tetrahedron (M_K = |K| M_ref), with extreme
+// eigenvalues 1/4 and 4.34747 (rounded up); Wathen's element argument bounds
+// the assembled (and Dirichlet-restricted) matrix by them
+constexpr double kMassVLow = 0.25;
+constexpr double kMassVHigh = 4.3475;
 
 template <class T> static inline const T* pick(const double* a, const float* b);
 template <> inline const double* pick<double>(const double* a, const float*) { return a; }
@@ -346,6 +352,7 @@ template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
   project_mean<T>(c, rp, np, kDotFast);
   mass_inverse<T>(c, rp, z1, c.opt.mass_steps);
   const bool lumped = c.opt.schur_prec == STOKES_SCHUR_PREC_LUMPED;
+  const bool vmass = c.opt.schur_prec == STOKES_SCHUR_PREC_MASS;
   const T* linv = pick<T>(c.lumped_inv64, c.lumped_inv32);
   int it = pcg<T>(
       c, np,
@@ -354,6 +361,14 @@ template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
           Tmp<T> t(c.pool, nv);
           bt_apply<T>(c.ex, c.Bt, p, t, linv, (const T*)nullptr, 1.0);
           b_apply<T>(c.ex, c.B, t, y, (const T*)nullptr, 1.0);
+        } else if (vmass) {
+          // B (M_V)_a^{-1} B^T p: a fixed Chebyshev polynomial in D^{-1} M_V
+          // (symmetric positive definite, so PCG stays valid)
+          Tmp<T> t(c.pool, nv), w(c.pool, nv);
+          bt_apply<T>(c.ex, c.Bt, p, t, (const T*)nullptr, (const T*)nullptr, 1.0);
+          cheb_run<T>(c, c.MV, 3, pick<T>(c.MV_dinv64, c.MV_dinv32), kMassVLow, kMassVHigh, c.opt.mass_steps_v, t,
+                      w, true, STOKES_KERNEL_SPMM_A3);
+          b_apply<T>(c.ex, c.B, w, y, (const T*)nullptr, 1.0);
         } else {
           spmv_store<T>(c.ex, c.LQ, 1, p, y, STOKES_KERNEL_SPMV_P1);
         }

@@ -160,3 +160,17 @@ def test_block_velocity_preconditioners_match_oracle(vel_prec, gamma, method):
 def test_block_velocity_preconditioners_mixed(vel_prec):
     r = run_case(8, 1e-2, 1e-3, 0.2, 2, gamma=1.0, tol=1e-8, precision=1, vel_prec=vel_prec)
     assert r["info"]["status"] == 0 and r["res"] <= 1.5e-8, r
+
+
+@pytest.mark.parametrize("steps,gamma,precision", [(8, 0.0, 0), (48, 1.0, 0), (8, 0.0, 1)])
+def test_schur_preconditioner_with_velocity_mass(steps, gamma, precision):
+    """C_lambda = mu (1 + gamma) M_Q^{-1} + dt^{-1} (B (M_V)_a^{-1} B^T)^{-1} with
+    (M_V)_a^{-1} a Chebyshev polynomial of 8 (economical) or 48 (~1e-10) steps."""
+    tol = 1e-12 if precision == 0 else 1e-8
+    r = run_case(6, 1e-2, 1e-3, 0.2, 15, gamma=gamma, tol=tol, g_seed=16, schur_prec=2, mass_steps_v=steps,
+                 precision=precision)
+    assert r["info"]["status"] == 0, r
+    if precision == 0:
+        assert r["eu"] <= PARITY and r["ep"] <= PARITY, r
+    else:
+        assert r["res"] <= 1.5e-8, r

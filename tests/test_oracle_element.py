@@ -130,3 +130,30 @@ def test_lumped_velocity_mass_constants():
         assert abs(val - LUMPED_REF[a]) < 1e-13, (a, val)
     # the signed vertex integral is negative, which is why the lumping uses |phi|
     assert abs(6 * np.sum(w * p2_eval(lam)[:, 1]) + 1 / 20) < 1e-14
+
+
+def test_jacobi_scaled_mass_intervals():
+    """Chebyshev-Jacobi on M_Q and M_V needs sigma(D^{-1} M). For affine
+    tetrahedra M_K = |K| M_ref, so the element pencil (M_K, diag M_K) has
+    shape-independent eigenvalues: P1 {1/2, 1/2, 1/2, 5/2} (Wathen 1987) and
+    for P2 extremes 1/4 and 4.34747. Wathen's element argument then bounds the
+    assembled, Dirichlet-restricted D^{-1} M; checked here on a jittered mesh."""
+    import scipy.linalg as sla
+    import workload as wl
+    from oracle.assemble import StokesSystem
+    from oracle.mesh import KuhnMesh
+    from oracle.reference_element import element_matrices
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((3, 4, 3))
+    em = element_matrices(X)
+    for t in range(3):
+        for M, lo, hi in ((em["mass"][t], 0.25, 4.347467), (em["pmass"][t], 0.5, 2.5)):
+            w = sla.eigh(M, np.diag(np.diag(M)), eigvals_only=True)
+            assert abs(w[0] - lo) < 1e-9 and abs(w[-1] - hi) < 1e-6, w
+    sysm = StokesSystem(KuhnMesh(3, wl.kuhn_vertices(3, 0.2, 1)), 1.0, 1.0)
+    Mv = sysm.Mv.toarray()[::3, ::3]                       # one velocity component
+    w = sla.eigh(Mv, np.diag(np.diag(Mv)), eigvals_only=True)
+    assert w[0] >= 0.25 - 1e-12 and w[-1] <= 4.3475, (w[0], w[-1])
+    Mq = sysm.MQ.toarray()
+    w = sla.eigh(Mq, np.diag(np.diag(Mq)), eigvals_only=True)
+    assert w[0] >= 0.5 - 1e-12 and w[-1] <= 2.5 + 1e-12
