@@ -502,6 +502,8 @@ stokes_status stokes_destroy(stokes_ctx* c) {
   for (auto& row : c->cgraph)
     for (auto& g : row)
       if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& kv : c->vgraphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->prof.reset();
   if (c->ev_read) cudaEventDestroy(c->ev_read);

@@ -6,7 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
@@ -429,6 +431,19 @@ struct stokes_ctx {
   // graphs are captured on this private stream (capture is not allowed on the
   // legacy default stream) and launched on ex.s
   cudaStream_t cap_stream = nullptr;
+  // whole V-cycles (all levels) replayed from graphs, keyed by (which, FP32,
+  // b, x, cycles): the vector pool hands the same buffers to the same call
+  // site, so a few keys recur. One private pool serves all of them (they run
+  // one at a time on ex.s). in_cycle_graph: a whole-cycle graph is being
+  // recorded or warmed, so nested V-cycle levels run as plain launches.
+  struct CycleGraph {
+    int seen = 0;
+    cudaGraphExec_t exec = nullptr;
+    sk::Prof::Counts counts;
+  };
+  std::map<std::tuple<int, int, const void*, void*, int>, CycleGraph> vgraphs;
+  sk::VecPool vgraph_pool;
+  bool in_cycle_graph = false;
   // counters
   int outer_iters = 0, inner_iters = 0, schur_inner_iters = 0;
   bool outer_capped = false, inner_capped = false;

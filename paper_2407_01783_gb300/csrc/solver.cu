@@ -123,7 +123,7 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
 // timed per class: under per-class profiling of a class that the coarse
 // levels launch, they run eagerly instead.
 static bool coarse_graph_ok(const stokes_ctx& c, int which) {
-  if (!c.opt.graphs || c.lv.size() < 2) return false;
+  if (!c.opt.graphs || c.lv.size() < 2 || c.in_cycle_graph) return false;
   if (!c.prof.on) return true;
   const int k = c.prof.only;
   if (k < 0) return false;
@@ -241,9 +241,98 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
   cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind);
 }
 
-template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
+template <class T> static void vcycles_plain(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
   vcycle<T>(c, which, 0, b, x, true);
   for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, b, x, false);
+}
+
+// A whole V-cycle in one graph needs every launch it makes to be untimed:
+// allowed without profiling, or when the one timed class is not launched by
+// a V-cycle of this kind.
+constexpr size_t kMaxCycleGraphs = 64;
+static bool cycle_graph_ok(const stokes_ctx& c, int which) {
+  if (!c.opt.graphs || c.in_cycle_graph) return false;
+  if (!c.prof.on) return true;
+  const int k = c.prof.only;
+  if (k < 0) return false;
+  const bool in_cycle = k == STOKES_KERNEL_TRANSFER || k == STOKES_KERNEL_BLAS1 || k == STOKES_KERNEL_OTHER ||
+                        k == STOKES_KERNEL_SPMM_A3_COARSE ||
+                        k == (which == 1 ? STOKES_KERNEL_SPMV_P1 : STOKES_KERNEL_SPMM_A3);
+  return !in_cycle;
+}
+
+// Whole V-cycles from graphs: the first call with a key runs plainly (all
+// levels, temporaries from the private pool), the second records the same
+// sequence on the capture stream, later calls replay it on ex.s.
+template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
+  if (!cycle_graph_ok(c, which)) {
+    vcycles_plain<T>(c, which, b, x, cycles);
+    return;
+  }
+  const auto key = std::make_tuple(which, (int)std::is_same<T, float>::value, (const void*)b, (void*)x, cycles);
+  auto it = c.vgraphs.find(key);
+  if (it == c.vgraphs.end()) {
+    if (c.vgraphs.size() >= kMaxCycleGraphs) {
+      vcycles_plain<T>(c, which, b, x, cycles);
+      return;
+    }
+    it = c.vgraphs.emplace(key, stokes_ctx::CycleGraph{}).first;
+  }
+  auto& G = it->second;
+  if (!c.vgraph_pool.arena) c.vgraph_pool.arena = &c.arena;
+  if (!G.exec) {
+    PoolSwap swap(c.pool, c.vgraph_pool);
+    c.in_cycle_graph = true;
+    if (G.seen == 0) {
+      try {
+        vcycles_plain<T>(c, which, b, x, cycles);
+      } catch (...) {
+        c.in_cycle_graph = false;
+        throw;
+      }
+      c.in_cycle_graph = false;
+      G.seen = 1;
+      return;
+    }
+    if (!c.cap_stream) {
+      c.in_cycle_graph = false;
+      SK_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+      c.in_cycle_graph = true;
+    }
+    G.counts = Prof::Counts{};
+    const cudaStream_t launch = c.ex.s;
+    cudaGraph_t g = nullptr;
+    cudaError_t e0 = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e0 != cudaSuccess) {
+      c.in_cycle_graph = false;
+      SK_CUDA(e0);
+    }
+    c.prof.capture = &G.counts;
+    c.ex.s = c.cap_stream;
+    try {
+      vcycles_plain<T>(c, which, b, x, cycles);
+    } catch (...) {
+      c.ex.s = launch;
+      c.prof.capture = nullptr;
+      c.in_cycle_graph = false;
+      cudaStreamEndCapture(c.cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    c.ex.s = launch;
+    c.prof.capture = nullptr;
+    c.in_cycle_graph = false;
+    SK_CUDA(cudaStreamEndCapture(c.cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    SK_CUDA(e);
+  }
+  SK_CUDA(cudaGraphLaunch(G.exec, c.ex.s));
+  if (c.prof.on)
+    for (int k = 0; k < STOKES_KERNEL_COUNT; ++k) {
+      c.prof.rec[k].launches += G.counts.launches[k];
+      c.prof.rec[k].bytes += G.counts.bytes[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
