@@ -261,19 +261,16 @@ static bool cycle_graph_ok(const stokes_ctx& c, int which) {
   return !in_cycle;
 }
 
-// Whole V-cycles from graphs: the first call with a key runs plainly (all
-// levels, temporaries from the private pool), the second records the same
-// sequence on the capture stream, later calls replay it on ex.s.
-template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
-  if (!cycle_graph_ok(c, which)) {
-    vcycles_plain<T>(c, which, b, x, cycles);
-    return;
-  }
-  const auto key = std::make_tuple(which, (int)std::is_same<T, float>::value, (const void*)b, (void*)x, cycles);
+// Sync-free regions (a whole V-cycle; C with fixed inner iterations) from
+// graphs keyed by their buffers: the first call with a key runs plainly
+// (temporaries from the private pool), the second records the same sequence
+// on the capture stream, later calls replay it on ex.s.
+using GraphKey = std::tuple<int, int, const void*, void*, int>;
+template <class Body> static void graph_region(stokes_ctx& c, const GraphKey& key, Body&& body) {
   auto it = c.vgraphs.find(key);
   if (it == c.vgraphs.end()) {
     if (c.vgraphs.size() >= kMaxCycleGraphs) {
-      vcycles_plain<T>(c, which, b, x, cycles);
+      body();
       return;
     }
     it = c.vgraphs.emplace(key, stokes_ctx::CycleGraph{}).first;
@@ -281,47 +278,35 @@ template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* 
   auto& G = it->second;
   if (!c.vgraph_pool.arena) c.vgraph_pool.arena = &c.arena;
   if (!G.exec) {
+    if (!c.cap_stream) SK_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
     PoolSwap swap(c.pool, c.vgraph_pool);
-    c.in_cycle_graph = true;
+    struct Flag {  // nested regions run plainly while this one is warmed or recorded
+      bool& f;
+      explicit Flag(bool& x) : f(x) { f = true; }
+      ~Flag() { f = false; }
+    } flag(c.in_cycle_graph);
     if (G.seen == 0) {
-      try {
-        vcycles_plain<T>(c, which, b, x, cycles);
-      } catch (...) {
-        c.in_cycle_graph = false;
-        throw;
-      }
-      c.in_cycle_graph = false;
+      body();
       G.seen = 1;
       return;
-    }
-    if (!c.cap_stream) {
-      c.in_cycle_graph = false;
-      SK_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
-      c.in_cycle_graph = true;
     }
     G.counts = Prof::Counts{};
     const cudaStream_t launch = c.ex.s;
     cudaGraph_t g = nullptr;
-    cudaError_t e0 = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e0 != cudaSuccess) {
-      c.in_cycle_graph = false;
-      SK_CUDA(e0);
-    }
+    SK_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
     c.prof.capture = &G.counts;
     c.ex.s = c.cap_stream;
     try {
-      vcycles_plain<T>(c, which, b, x, cycles);
+      body();
     } catch (...) {
       c.ex.s = launch;
       c.prof.capture = nullptr;
-      c.in_cycle_graph = false;
       cudaStreamEndCapture(c.cap_stream, &g);
       if (g) cudaGraphDestroy(g);
       throw;
     }
     c.ex.s = launch;
     c.prof.capture = nullptr;
-    c.in_cycle_graph = false;
     SK_CUDA(cudaStreamEndCapture(c.cap_stream, &g));
     cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
     cudaGraphDestroy(g);
@@ -333,6 +318,15 @@ template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* 
       c.prof.rec[k].launches += G.counts.launches[k];
       c.prof.rec[k].bytes += G.counts.bytes[k];
     }
+}
+
+template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
+  if (!cycle_graph_ok(c, which)) {
+    vcycles_plain<T>(c, which, b, x, cycles);
+    return;
+  }
+  graph_region(c, GraphKey(which, (int)std::is_same<T, float>::value, (const void*)b, (void*)x, cycles),
+               [&]() { vcycles_plain<T>(c, which, b, x, cycles); });
 }
 
 // ---------------------------------------------------------------------------
@@ -434,7 +428,7 @@ template <class T> static int ainv(stokes_ctx& c, const T* t, T* w, double tol) 
 //   V-cycle of eps M_Q + L_Q as preconditioner (Sec. 4.2), on the complement
 //   of the constants.
 // ---------------------------------------------------------------------------
-template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
+template <class T> static int cprec_body(stokes_ctx& c, const T* r, T* z) {
   size_t np = npres(c), nv = nvel(c);
   Tmp<T> rp(c.pool, np), z1(c.pool, np), z2(c.pool, np);
   copy<T>(c, rp, r, np);
@@ -470,8 +464,30 @@ template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
         vcycles<T>(c, 1, vp, w, 1);
       },
       (const T*)rp, (T*)z2, c.opt.schur_inner_tol, c.opt.max_inner, nullptr, c.opt.schur_inner_iters);
-  c.schur_inner_iters += it;
   lincomb2<T>(c.ex, np, c.mu * (1.0 + c.gamma), z1, 1.0 / c.dt, z2, z);
+  return it;
+}
+
+// With a fixed number of inner iterations C has no host synchronisation, so it
+// is replayed from a graph (keyed by r, z and the device-scalar stack depth,
+// whose slots it uses) when none of its launches is being timed per class.
+static bool cprec_graph_ok(const stokes_ctx& c) {
+  if (!c.opt.graphs || c.in_cycle_graph || c.opt.schur_inner_iters <= 0) return false;
+  if (!c.prof.on) return true;
+  const int k = c.prof.only;
+  if (k < 0) return false;
+  return k == STOKES_KERNEL_SPMV_A || k == STOKES_KERNEL_RESIDUAL || k == STOKES_KERNEL_SPMM_A3_COARSE ||
+         (k == STOKES_KERNEL_SPMM_A3 && c.opt.schur_prec != STOKES_SCHUR_PREC_MASS);
+}
+
+template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
+  if (!cprec_graph_ok(c)) {
+    c.schur_inner_iters += cprec_body<T>(c, r, z);
+    return;
+  }
+  c.schur_inner_iters += c.opt.schur_inner_iters;  // fixed iterations: known without running
+  graph_region(c, GraphKey(16 + (int)std::is_same<T, float>::value, 0, (const void*)r, (void*)z, c.sc.top),
+               [&]() { (void)cprec_body<T>(c, r, z); });
 }
 
 // ---------------------------------------------------------------------------
