@@ -456,7 +456,7 @@ def run_batched(sk, torch, wl, dev, world, dist, count=32, rhs=4):
             "worst_residual": max(x["rel_residual"] for x in flat),
             "failed": sum(1 for x in flat if x["status"] != 0),
             "scheme": "one context + stream per instance, host thread per instance, mixed precision, "
-                      "coupled FGMRES(30) + block-LU, coarse V-cycle levels from CUDA graphs"}
+                      "coupled FGMRES(30) + block-LU, V-cycles replayed from CUDA graphs"}
 
 
 def run_coupled96(sk, torch, wl, dev, world, dist, n=96, mu=1e-3, dt=1e-3, gammas=(0.0, 1.0, 10.0), seed=3):
