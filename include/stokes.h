@@ -34,6 +34,12 @@
  *    and work space and frees them in stokes_destroy.
  *  - Every call returns a stokes_status; none aborts, traps or prints. On
  *    error, stokes_last_error() describes the cause (per thread).
+ *  - A context is used by one host thread at a time; separate contexts may
+ *    run concurrently (own streams, own host threads).
+ *  - With options.graphs = 1 a context records its V-cycles (and C, when its
+ *    inner solve has a fixed iteration count) into CUDA graphs the second
+ *    time it meets the same buffers, on a private stream, and replays them
+ *    on its stream afterwards; results are bitwise those of plain launches.
  */
 #ifndef STOKES_H
 #define STOKES_H
