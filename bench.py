@@ -263,6 +263,8 @@ def run_ours(args):
             opt = sk.stokes_default_options(precision=precision, profile=profile, vcycles=args.vcycles,
                                             schur_inner_iters=args.schur_inner_iters, format=args.format,
                                             vel_prec=args.vel_prec, schur_prec=args.schur_prec,
+                                            **({"inner_tol": args.inner_tol} if args.inner_tol else {}),
+                                            **({"pass_tol": args.pass_tol} if args.pass_tol else {}),
                                             **extra)
             S = sk.Stokes(n, V, mu, DT, 0.0, opt, device=dev)
             f = torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev)
@@ -539,6 +541,8 @@ def main():
     ap.add_argument("--no-coupled96", action="store_true", help="skip the 96^3 coupled-vs-Schur comparison")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
+    ap.add_argument("--inner-tol", type=float, default=None, help="override options.inner_tol")
+    ap.add_argument("--pass-tol", type=float, default=None, help="override options.pass_tol")
     ap.add_argument("--schur-prec", type=int, default=0, choices=[0, 1, 2],
                     help="Schur preconditioner C^Lambda (default), C^Delta or C_lambda (M_V)")
     ap.add_argument("--vel-prec", type=int, default=3, choices=[1, 2, 3],
