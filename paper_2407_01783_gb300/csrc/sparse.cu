@@ -466,31 +466,23 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
   st_coords(a, c, r, i, qx, qy, qz);
   if (i >= a.ext[c][0]) return;  // padding row
   const int row = st_index(a, qx, qy, qz);
-  const bool inner = qy - 2 >= a.lo && qy + 2 <= a.hi && qz - 2 > a.lo && qz + 2 < a.hi;
   T acc[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc[q] = T(0);
   const TM* vr = v + a.voff[c] + r;
   const size_t rc = (size_t)a.prows[c];
   const int S = a.S[c], db = a.dbeg[c];
-  if (inner) {
+  // Entries whose neighbour lies outside the index space are stored as 0; their
+  // linear index may fall on another node or, near the first and last planes,
+  // outside the vector, so it is clamped into [0, xs): every row takes the same
+  // branch-free loop and the zero weight cancels the clamped read.
+  const int last = (int)xs - 1;
 #pragma unroll 4
-    for (int e = 0; e < S; ++e) {
-      const T w = (T)__ldcs(&vr[e * rc]);  // streamed once: evict first
-      const size_t cc = (size_t)(row + a.lin[db + e]);
+  for (int e = 0; e < S; ++e) {
+    const T w = (T)__ldcs(&vr[e * rc]);  // streamed once: evict first
+    const size_t cc = (size_t)min(max(row + a.lin[db + e], 0), last);
 #pragma unroll
-      for (int q = 0; q < NR; ++q) acc[q] += w * x[q * xs + cc];
-    }
-  } else {
-#pragma unroll 4
-    for (int e = 0; e < S; ++e) {
-      const int de = db + e;
-      const bool ok = st_inside(a, qx + a.d[de][0], qy + a.d[de][1], qz + a.d[de][2]);
-      const T w = ok ? (T)__ldcs(&vr[e * rc]) : T(0);
-      const size_t cc = (size_t)(ok ? row + a.lin[de] : row);
-#pragma unroll
-      for (int q = 0; q < NR; ++q) acc[q] += w * x[q * xs + cc];
-    }
+    for (int q = 0; q < NR; ++q) acc[q] += w * x[q * xs + cc];
   }
   epi(row, acc);
 }
