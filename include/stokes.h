@@ -108,10 +108,12 @@ typedef struct {
   int format;            /* 0: stencil-structured storage for A~_3, eps M_Q + L_Q,
                             M_Q, L_Q on levels with >= 2^18 rows, CSR below;
                             1: CSR everywhere; 2: stencil storage on every level */
-  int graphs;            /* 1 (default): levels >= 1 of each V-cycle are replayed
-                            from a CUDA graph captured on the context's stream
-                            at the second V-cycle (the first runs them eagerly);
-                            0: plain launches */
+  int graphs;            /* 1 (default): V-cycles, and C when schur_inner_iters
+                            > 0, are recorded into CUDA graphs on a private
+                            stream the second time the same buffers come by and
+                            replayed on the context's stream afterwards (while
+                            finest-level launches are timed per class, only
+                            levels >= 1 are); 0: plain launches */
   int vel_prec;          /* velocity preconditioner inside A^{-1} solves and the
                             block preconditioners (Sec. 5.1, Eqs.
                             precond_A_plus_lambda_D_1..3): 3 (default) A~_3 =
