@@ -14,7 +14,9 @@ from __future__ import annotations
 import numpy as np
 
 from .mesh import KuhnMesh
-from .reference_element import P2_MASS_REF, element_matrices
+from .quadrature import reference_tet_rule
+from .reference_element import (MOMENT2, P2_MASS_REF, element_matrices, p2_eval,
+                                p2_gradient_coefficients, tet_geometry)
 
 
 def node_to_tets(mesh: KuhnMesh, nodes: np.ndarray, vertex: bool = False):
@@ -79,3 +81,102 @@ def load_norm(mesh: KuhnMesh, f_nodal, chunk: int = 20000) -> float:
         for c in range(3):
             F[:, c] += np.bincount(gl.ravel(), weights=contrib[:, :, c].ravel(), minlength=mesh.n_p2)
     return float(np.linalg.norm(F[mesh.interior]))
+
+
+def _chunk_geometry(mesh: KuhnMesh, s: int, e: int):
+    """|K| and the gradient coefficients W (T, 10, 4, 3) of tets s..e-1:
+    grad phi_a = sum_i lam_i W[a, i, :] on each tet."""
+    vol, _, G = tet_geometry(mesh.coords[s:e])
+    return vol, p2_gradient_coefficients(G)
+
+
+def full_residual(mesh: KuhnMesh, mu: float, dt: float, f_nodal, cases, chunk: int = 50000):
+    """Every row of r = [F - A U + B^T P ; g - B U] for several (u, p, g).
+
+    A = M_V/dt + mu E_V and B_kj = int psi_k div phi_j are the operators of the
+    saddle system (Sec. 2.2, Eq. Saddle_point_A_BT_B), F = M_V f_h. Each row
+    is a sum of element contributions, evaluated here tet by tet in vectorised
+    chunks without forming any global matrix, from the gradients of the P2
+    functions (linear on an affine tet) and the exact barycentric moments:
+      int_K 2 eps(u_h) : eps(phi_a e_c) = |K| sum_{i,d} W[a,i,d] (Q[i,d,c] + Q[i,c,d]),
+      Q[i,d,e] = sum_k M2[i,k] sum_b W[b,k,d] u_b,e   (M2[i,k] = int lam_i lam_k / |K|),
+      int_K psi_k div(u_h)       = |K| sum_i M2[k,i] sum_d Q'[i,d,d],
+      int_K p_h div(phi_a e_c)   = |K| sum_i (sum_k p_k M2[k,i]) W[a,i,c].
+    `f_nodal` (n_p2, 3) is one force for all cases or a list with one per
+    case; `cases` is a list of (u_nodal (n_p2, 3) with
+    zero boundary rows, p (n_p1,), g (n_p1,) or None). Returns a list of
+    (rF (n_interior, 3), rg (n_p1,)) and ||[F; g]|| per case.
+    """
+    npv, npp = mesh.n_p2, mesh.n_p1
+    forces = list(f_nodal) if isinstance(f_nodal, (list, tuple)) else [f_nodal] * len(cases)
+    assert len(forces) == len(cases)
+    R = [np.zeros((npv, 3)) for _ in cases]
+    Fs = [np.zeros((npv, 3)) for _ in cases]
+    BU = [np.zeros(npp) for _ in cases]
+    for s in range(0, mesh.n_tets, chunk):
+        e = min(s + chunk, mesh.n_tets)
+        vol, W = _chunk_geometry(mesh, s, e)
+        gl = mesh.tet_p2[s:e]                       # (T, 10)
+        gv = mesh.tet_vertices[s:e]                 # (T, 4)
+        T = e - s
+        Wf = W.reshape(T, 10, 12)                                        # (a, (i, d))
+        for j, (u_nodal, p, _) in enumerate(cases):
+            fl = np.einsum("ab,tbc->tac", P2_MASS_REF, forces[j][gl], optimize=True) * vol[:, None, None]
+            ul = u_nodal[gl]                                             # (T, 10, 3)
+            # gradu[k, d, e]: d_d u_e = sum_k lam_k gradu[k, d, e]
+            gradu = np.matmul(np.swapaxes(Wf, 1, 2), ul).reshape(T, 4, 3, 3)
+            Q = np.einsum("ik,tkde->tide", MOMENT2, gradu, optimize=True)
+            S2 = (Q + np.swapaxes(Q, 2, 3)).reshape(T, 12, 3)            # ((i, d), c)
+            strain = np.matmul(Wf, S2) * vol[:, None, None]
+            mass = np.einsum("ab,tbc->tac", P2_MASS_REF, ul, optimize=True) * vol[:, None, None]
+            au = mass / dt + mu * strain
+            pm = p[gv] @ MOMENT2                                         # (T, 4), M2 symmetric
+            btp = np.einsum("ti,taic->tac", pm, W, optimize=True) * vol[:, None, None]
+            divu = np.einsum("tidd->ti", Q)                              # int lam_i div u_h / |K|
+            bu = divu * vol[:, None]
+            loc = fl - au + btp                                          # F - A U + B^T P
+            for c in range(3):
+                R[j][:, c] += np.bincount(gl.ravel(), weights=loc[:, :, c].ravel(), minlength=npv)
+                Fs[j][:, c] += np.bincount(gl.ravel(), weights=fl[:, :, c].ravel(), minlength=npv)
+            BU[j] += np.bincount(gv.ravel(), weights=bu.ravel(), minlength=npp)
+    inner = mesh.interior
+    out = []
+    for j, (_, _, g) in enumerate(cases):
+        gg = np.zeros(npp) if g is None else np.asarray(g, dtype=float)
+        rF = R[j][inner]
+        rg = gg - BU[j]
+        norm = float(np.sqrt(np.sum(Fs[j][inner] ** 2) + np.sum(gg ** 2)))
+        out.append((rF, rg, norm))
+    return out
+
+
+def relative_residuals(mesh: KuhnMesh, mu: float, dt: float, f_nodal, cases, chunk: int = 50000):
+    """||[F - A U + B^T P; g - B U]||_2 / ||[F; g]||_2 per case (see full_residual)."""
+    res = []
+    for rF, rg, norm in full_residual(mesh, mu, dt, f_nodal, cases, chunk):
+        res.append(float(np.sqrt(np.sum(rF ** 2) + np.sum(rg ** 2)) / norm))
+    return res
+
+
+def l2_errors_chunked(mesh: KuhnMesh, u_nodal, p, exact, q: int = 4, chunk: int = 20000):
+    """Relative L2 errors ||u - u_h|| / ||u||, ||p - p_h|| / ||p|| by the conical
+    Gauss rule with q points per direction, tet by tet in chunks (the same
+    definition as oracle.solve.l2_errors, for meshes too large to assemble)."""
+    lam, w = reference_tet_rule(q)
+    phi = p2_eval(lam)
+    num_u = den_u = num_p = den_p = 0.0
+    for s in range(0, mesh.n_tets, chunk):
+        e = min(s + chunk, mesh.n_tets)
+        X = mesh.coords[s:e]
+        vol, _, _ = tet_geometry(X)
+        wts = 6.0 * vol[:, None] * w[None, :]
+        Xq = np.einsum("qi,tic->tqc", lam, X).reshape(-1, 3)
+        uh = np.einsum("qa,tac->tqc", phi, u_nodal[mesh.tet_p2[s:e]])
+        ph = np.einsum("qi,ti->tq", lam, p[mesh.tet_vertices[s:e]])
+        ue = exact.velocity(Xq).reshape(uh.shape)
+        pe = exact.pressure(Xq).reshape(ph.shape)
+        num_u += float(np.sum(wts[..., None] * (ue - uh) ** 2))
+        den_u += float(np.sum(wts[..., None] * ue ** 2))
+        num_p += float(np.sum(wts * (pe - ph) ** 2))
+        den_p += float(np.sum(wts * pe ** 2))
+    return float(np.sqrt(num_u / den_u)), float(np.sqrt(num_p / den_p))

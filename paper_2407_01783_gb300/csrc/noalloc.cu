@@ -12,7 +12,9 @@
 // needs clearing. Calls whose kernels overlap on the GPU (for example two
 // streams, or two contexts used from two threads at once) race on the array.
 #include <cmath>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <string>
 
 #include "internal.h"
@@ -51,6 +53,7 @@ cudaError_t scratch_address(double** out) {
 
 extern "C" stokes_status stokes_apply_agamma_noalloc(stokes_ctx* c, const double* x, double* y) {
   using namespace sk;
+  set_last_error("");
   if (!c || !x || !y) {
     set_last_error("stokes_apply_agamma_noalloc: null argument");
     return STOKES_ERR_ARG;
@@ -104,6 +107,15 @@ extern "C" stokes_status stokes_apply_agamma_noalloc(stokes_ctx* c, const double
   } catch (const sk::Error& e) {
     set_last_error(e.what());
     return (stokes_status)e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("stokes_apply_agamma_noalloc: host allocation failed");
+    return STOKES_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_last_error(std::string("stokes_apply_agamma_noalloc: ") + e.what());
+    return STOKES_ERR_CUDA;
+  } catch (...) {
+    set_last_error("stokes_apply_agamma_noalloc: unknown exception");
+    return STOKES_ERR_CUDA;
   }
   return STOKES_OK;
 }

@@ -88,18 +88,55 @@ def test_one_level_vcycle_is_exact_inverse():
     S.close()
 
 
-@pytest.mark.parametrize("gamma", [0.0, 1.0, 10.0])
-def test_largest_configuration_coupled_96(gamma):
-    """96^3 jittered mesh (22.5 M DOFs), block-triangular FGMRES(30) on the
-    coupled system with augmented Lagrangian gamma, mixed precision: the
-    largest configuration solves to 1e-8."""
-    sk = gpu_module()
+@pytest.fixture(scope="module")
+def coupled96():
     n, mu, dt = 96, 1e-3, 1e-3
     V = wl.kuhn_vertices(n, 0.2, 3)
-    f = wl.manufactured_force(n, V, mu, dt, 3)
+    return n, mu, dt, V, KuhnMesh(n, V), wl.manufactured_force(n, V, mu, dt, 3)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 1.0, 10.0])
+def test_largest_configuration_coupled_96(coupled96, gamma):
+    """96^3 jittered mesh (22.5 M DOFs), block-triangular FGMRES(30) on the
+    coupled system with augmented Lagrangian gamma, mixed precision. Every
+    row of the residual of the original saddle system (the augmented form has
+    the same solution) is evaluated by the oracle's element loop and must meet
+    the tolerance, in agreement with the GPU's own FP64 residual."""
+    from oracle.local import relative_residuals
+    sk = gpu_module()
+    n, mu, dt, V, mesh, f = coupled96
     S = sk.Stokes(n, V, mu, dt, gamma, sk.stokes_default_options(precision=1, vcycles=1, method=1, block_lu=0))
     assert S.sizes["dofs"] == 21567171 + 912673
     u, p, info = S.solve(cuda(f), None, 1e-8)
     assert info.status == 0 and info.rel_residual <= 1e-8, info.as_dict()
-    assert np.isfinite(host(p)).all()
+    uh, ph = host(u), host(p)
     S.close()
+    rel = relative_residuals(mesh, mu, dt, f, [(uh, ph, None)])[0]
+    print(f"96^3 gamma={gamma:g}: oracle residual {rel:.3e}, GPU residual {info.rel_residual:.3e}")
+    assert rel <= 1e-8 * (1 + 1e-6) and abs(rel - info.rel_residual) <= 1e-11, (rel, info.rel_residual)
+
+
+def test_largest_configuration_manufactured_errors_96(coupled96):
+    """Discretisation error of the GPU's 96^3 solution against the manufactured
+    (u, p), next to the 48^3 solution of the same problem: velocity L2 error
+    O(h^3) and pressure O(h^2) (Sec. 3.3) between the two meshes, evaluated by
+    the oracle's chunked quadrature."""
+    from oracle.local import l2_errors_chunked
+    sk = gpu_module()
+    n, mu, dt, V, mesh, f = coupled96
+    errs = []
+    for m, Vm, msh, fm in ((48, None, None, None), (n, V, mesh, f)):
+        if Vm is None:
+            Vm = wl.kuhn_vertices(m, 0.2, 3)
+            msh = KuhnMesh(m, Vm)
+            fm = wl.manufactured_force(m, Vm, mu, dt, 3)
+        S = sk.Stokes(m, Vm, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1, method=1, block_lu=0))
+        u, p, info = S.solve(cuda(fm), None, 1e-10)
+        assert info.status == 0
+        uh, ph = host(u), host(p)
+        S.close()
+        errs.append(l2_errors_chunked(msh, uh, ph, wl.Manufactured(3), q=3))
+    ru = np.log2(errs[0][0] / errs[1][0])
+    rp = np.log2(errs[0][1] / errs[1][1])
+    print(f"manufactured L2 errors 48^3 {errs[0]}, 96^3 {errs[1]}: rates velocity {ru:.2f}, pressure {rp:.2f}")
+    assert ru > 2.65 and rp > 1.65, (errs, ru, rp)

@@ -2,40 +2,38 @@
 
 The 48^3 jittered workload (seed 2, dt = 1e-3, mixed precision, one V-cycle)
 is solved on the GPU to a true relative residual of 1e-8. The oracle cannot
-solve it, but it evaluates residual rows at sampled nodes from the incident
-elements (oracle.local, pinned against the global assembly). Because
-|r_i| <= ||r||_2 <= tol ||[F; g]||_2 holds for every row, each sampled row is
-checked against that bound, and the sampled rows' root mean square (scaled to
-the full row count) is checked against the tolerance as well.
+solve it directly, but it evaluates EVERY row of the residual
+r = [F - A U + B^T P ; g - B U] of the GPU's (U, P) from its own element loop
+(oracle.local.full_residual, pinned against the global assembly on small
+meshes), so the acceptance test of Eq. Saddle_point_A_BT_B is checked
+independently of the GPU's own residual evaluation. The mixed-precision
+solution's error is stated against an FP64 solve of the same system to 1e-12,
+itself checked by the oracle's residual.
 """
 
 import numpy as np
 import pytest
 
 import workload as wl
-from oracle.local import load_norm, pressure_residual_rows, velocity_residual_rows
+from oracle.local import relative_residuals
 from oracle.mesh import KuhnMesh
 
-from gpu_helpers import cuda, gpu_module, host
+from gpu_helpers import cuda, gpu_module, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-8
+# the oracle and the GPU evaluate the same residual in different summation
+# orders: they agree to rounding (~1e-13 relative to ||[F; g]||), far below TOL
+AGREE = 1e-11
 
 
-def sampled_check(n, V, mu, dt, f, u, p, mesh, seed=0, kv=160, kp=80):
-    rng = np.random.default_rng(seed)
-    vel_nodes = rng.choice(mesh.interior, kv, replace=False)
-    vel_nodes[:8] = mesh.interior[:8]              # include nodes next to the boundary
-    p_nodes = rng.choice(mesh.n_p1, kp, replace=False)
-    rv = velocity_residual_rows(mesh, mu, dt, f, u, p, vel_nodes)
-    rp = pressure_residual_rows(mesh, u, None, p_nodes)
-    normF = load_norm(mesh, f)
-    bound = TOL * normF
-    assert np.abs(rv).max() <= bound and np.abs(rp).max() <= bound, (np.abs(rv).max(), np.abs(rp).max(), bound)
-    nrows = 3 * mesh.interior.size + mesh.n_p1
-    est = np.sqrt((np.sum(rv ** 2) + np.sum(rp ** 2)) / (rv.size + rp.size) * nrows) / normF
-    return est
+def oracle_check(mesh, mu, dt, f, u, p, info, tol=TOL, g=None):
+    rel = relative_residuals(mesh, mu, dt, f, [(host(u), host(p), g)])[0]
+    print(f"n={mesh.n} mu={mu:g}: oracle residual {rel:.3e}, GPU residual {info.rel_residual:.3e}")
+    assert rel <= tol * (1 + 1e-6), (rel, tol)
+    assert abs(rel - info.rel_residual) <= AGREE, (rel, info.rel_residual)
+    return rel
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +45,9 @@ def workload48():
 
 @pytest.mark.parametrize("imu", [0, 1, 2])
 def test_bench_workload_method1_mixed(workload48, imu):
+    """Benchmark configuration (Schur CG + C^Lambda, mixed precision, 1 V-cycle):
+    every residual row checked by the oracle; the error against an FP64 GPU
+    solve to 1e-12 (also oracle-checked) is stated."""
     sk = gpu_module()
     n, V, mus, dt, mesh = workload48
     mu = mus[imu]
@@ -54,9 +55,16 @@ def test_bench_workload_method1_mixed(workload48, imu):
     S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1))
     u, p, info = S.solve(cuda(f), None, TOL)
     assert info.status == 0 and info.rel_residual <= TOL
-    est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=imu)
-    assert est <= 2 * TOL, est
+    oracle_check(mesh, mu, dt, f, u, p, info)
     S.close()
+    S64 = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(vcycles=1))
+    u64, p64, info64 = S64.solve(cuda(f), None, 1e-12)
+    assert info64.status == 0
+    oracle_check(mesh, mu, dt, f, u64, p64, info64, tol=1e-12)
+    S64.close()
+    eu, ep = rel_err(host(u), host(u64)), rel_err(host(p), host(p64))
+    print(f"mixed-precision error vs FP64 (1e-12) at mu={mu:g}: velocity {eu:.2e}, pressure {ep:.2e}")
+    assert eu < 1e-4 and ep < 1e-3, (eu, ep)
 
 
 def test_bench_workload_method2_mixed(workload48):
@@ -67,21 +75,20 @@ def test_bench_workload_method2_mixed(workload48):
     S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1, method=1))
     u, p, info = S.solve(cuda(f), None, TOL)
     assert info.status == 0 and info.rel_residual <= TOL
-    est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=7)
-    assert est <= 2 * TOL, est
+    oracle_check(mesh, mu, dt, f, u, p, info)
     S.close()
 
 
-def test_bench_workload_random_rhs(workload48):
-    """The 48^3 workload with an N(0, 1) nodal body force (seed 2) instead of the
-    manufactured one: rough right-hand side, same tolerance, sampled rows."""
+def test_bench_workload_random_rhs_with_pressure_load(workload48):
+    """The 48^3 workload with an N(0, 1) nodal body force and a compatible
+    pressure load g (sum g = 0): rough right-hand side, same tolerance."""
     sk = gpu_module()
     n, V, mus, dt, mesh = workload48
     mu = 1e-2
     f = wl.random_force(n, 2)
+    g = wl.random_pressure_load(n, 2)
     S = sk.Stokes(n, V, mu, dt, 0.0, sk.stokes_default_options(precision=1, vcycles=1))
-    u, p, info = S.solve(cuda(f), None, TOL)
+    u, p, info = S.solve(cuda(f), cuda(g), TOL)
     assert info.status == 0 and info.rel_residual <= TOL
-    est = sampled_check(n, V, mu, dt, f, host(u), host(p), mesh, seed=11)
-    assert est <= 2 * TOL, est
+    oracle_check(mesh, mu, dt, f, u, p, info, g=g)
     S.close()

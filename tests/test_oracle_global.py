@@ -186,3 +186,45 @@ def test_cahouet_chabard_limits():
     # C (with M_V) is exact in the mu -> 0 limit
     ev = preconditioned_spectrum(preconditioner(small, "mass"), S0)
     assert ev[-1] / ev[0] < 1 + 1e-3
+
+
+def test_pressure_laplacian_preconditioner_bounds():
+    """C^Delta_lambda = dt^{-1} L_Q^+ + mu (1+lambda) M_Q^{-1} (Eqs.
+    Schur_complement_preconditioners, pressure-Laplacian form) against bounds
+    that follow from the continuous operators, not from its own formula:
+    * (div v, q) = -(v, grad q) for v in H^1_0 gives q^T B M_V^{-1} B^T q <=
+      q^T L_Q q, so in the limit mu dt / h^2 -> 0 (S -> dt B M_V^{-1} B^T) every
+      eigenvalue of C^Delta S is <= 1;
+    * ||div v||^2 <= ||eps(v)||^2 = v^T E_V v / 2 on H^1_0 gives
+      M_Q^{-1} B E_V^{-1} B^T <= 1/2, so as mu dt / h^2 -> infinity
+      (mu S -> B E_V^{-1} B^T) the eigenvalues are <= 1/2;
+    * S <= both limits, hence lambda_max(C^Delta S) <= 3/2 for every mu, dt;
+    * with the augmented Lagrangian, S_lambda^+ = S^+ + lambda mu M_Q^{-1}, so as
+      lambda -> infinity C^Delta_lambda S_lambda -> (1+lambda)/lambda -> 1.
+    A wrong dt or mu scaling, a missing (1+lambda) or M_Q in place of M_Q^{-1}
+    breaks one of these. On the unjittered Kuhn mesh the interior rows of L_Q
+    are h times the 7-point finite-difference Laplacian (a closed form)."""
+    for n in (2, 3):
+        for mu in 10.0 ** np.arange(-8, 7, 2):
+            s = build(n, mu=mu, dt=1e-2)
+            ev = preconditioned_spectrum(preconditioner(s, "laplace"), schur(s))
+            assert ev[0] > 0 and ev[-1] <= 1.5 + 1e-10, (n, mu, ev[-1])
+            if mu <= 1e-6:
+                assert ev[-1] <= 1.0 + 1e-6, (n, mu, ev[-1])
+            if mu >= 1e4:
+                assert ev[-1] <= 0.5 + 1e-6, (n, mu, ev[-1])
+    s = build(2, mu=0.3, dt=1e-2)
+    ev = preconditioned_spectrum(preconditioner(s, "laplace", 1e6), schur(s, 1e6))
+    assert abs(ev[0] - 1) < 1e-4 and abs(ev[-1] - 1) < 1e-4, (ev[0], ev[-1])
+    # closed form of L_Q on the unjittered Kuhn mesh
+    n = 3
+    s = build(n, jitter=0.0)
+    LQ = dense(s.LQ)
+    h, nv = 1.0 / n, n + 1
+    for (i, j, k) in ((1, 1, 1), (2, 1, 2), (1, 2, 2)):
+        v = i + nv * (j + nv * k)
+        ref = np.zeros(nv ** 3)
+        ref[v] = 6 * h
+        for d in (1, nv, nv * nv):
+            ref[v - d] = ref[v + d] = -h
+        assert np.abs(LQ[v] - ref).max() < 1e-13
