@@ -106,8 +106,15 @@ typedef struct {
                             its inner velocity solves get max(inner_tol,
                             pass_tol/30). Default 3e-2. */
   int format;            /* 0: stencil-structured storage for A~_3, eps M_Q + L_Q,
-                            M_Q, L_Q on levels with >= 2^18 rows, CSR below;
-                            1: CSR everywhere; 2: stencil storage on every level */
+                            M_Q, L_Q on levels with >= 2^18 rows, CSR below; the
+                            strain-form A in symmetric stencil storage (diagonal
+                            and upper 3x3 blocks only: half the matrix bytes)
+                            for its products and the double-float refinement
+                            residual;
+                            1: CSR everywhere (A as BSR3, CSR of 3x3 blocks);
+                            2: stencil storage on every level, A as in 0;
+                            3: as 0 but the products of A from BSR3 (the
+                            refinement residual still symmetric) */
   int graphs;            /* 1 (default): V-cycles, and C when schur_inner_iters
                             > 0, are recorded into CUDA graphs on a private
                             stream the second time the same buffers come by and
@@ -126,6 +133,26 @@ typedef struct {
                             (schur_prec = STOKES_SCHUR_PREC_MASS) on the exact
                             P2 interval [1/4, 4.3475]: 8 (default, the paper's
                             economical "2Vc" reading) ... 48 (~1e-10, "th") */
+  int coarse_kernel;     /* 1: the levels below the finest of each V-cycle of
+                            A~_3 and eps M_Q + L_Q run in one cooperative
+                            kernel (grid-wide barriers between the steps,
+                            bounded waits: STOKES_ERR_TIMEOUT if one expires);
+                            0 (default): one launch per step, replayed from a
+                            CUDA graph (faster on GB300 at 48^3: the barriers
+                            cost more than the launches they replace) */
+  int pass_schedule;     /* defect-correction schedule: 0 (default) = 1 for mixed
+                            precision, 2 for FP64; 1 = passes that each ask for a
+                            reduction of pass_tol with inner velocity solves at
+                            max(inner_tol, pass_tol/30); 2 = one pass aimed
+                            straight at tol with inner solves at inner_tol (the
+                            paper's setting) */
+  double cheb_low;       /* Chebyshev-Jacobi smoothing interval [cheb_low, */
+  double cheb_high;      /* cheb_high] x the Lanczos estimate of
+                            lambda_max(D^{-1} M) on every level (the paper
+                            names the smoother only): 0.1 and 1.1 by default.
+                            An interval far below the spectrum makes the
+                            V-cycle indefinite; the Krylov solvers then report
+                            STOKES_ERR_BREAKDOWN. */
 } stokes_options;
 
 typedef struct {
@@ -261,8 +288,9 @@ stokes_status stokes_matrix_export(stokes_ctx* ctx, int which, int level,
 /* Problem sizes: {n, levels, interior P2 nodes, P1 nodes, all P2 nodes, dofs}. */
 stokes_status stokes_sizes(stokes_ctx* ctx, int64_t sizes[6]);
 
-/* Per-kernel timing (options.profile = 1): kernel ids are STOKES_KERNEL_*.
- * Returns launches, summed CUDA-event milliseconds and algorithmic bytes
+/* Per-kernel statistics (options.profile != 0): kernel ids are STOKES_KERNEL_*.
+ * Returns all launches (graph replays included), the summed CUDA-event
+ * milliseconds of the timed ones and the algorithmic bytes of all launches
  * (matrix read once, each vector read/written once) since the last reset. */
 typedef enum {
   STOKES_KERNEL_SPMM_A3 = 0,      /* A~_3 x 3 RHS on the finest level (smoother/residual) */
@@ -275,13 +303,40 @@ typedef enum {
   STOKES_KERNEL_OTHER = 7,        /* load vectors, coarse solves, layouts   */
   STOKES_KERNEL_SPMM_A3_COARSE = 8, /* A~_3 x 3 RHS on the coarser levels   */
   STOKES_KERNEL_RESIDUAL = 9,     /* A U in the FP64 full-system residual    */
-  STOKES_KERNEL_COUNT = 10
+  STOKES_KERNEL_COARSE_CYCLE = 10,/* every level below the finest of a V-cycle
+                                     in one cooperative kernel               */
+  STOKES_KERNEL_COUNT = 11
 } stokes_kernel;
 stokes_status stokes_kernel_stats(stokes_ctx* ctx, int kernel, int64_t* launches,
                                   double* total_ms, double* bytes);
+/* The launches of a class that were bracketed by CUDA events since the last
+ * reset (all of them with profile = 1, which runs without graphs; with
+ * profile = 2 + k the graphs stay on and only class k's launches outside graph
+ * replays are timed), their summed milliseconds and algorithmic bytes, so that
+ * timed_bytes / timed_ms is the class's achieved bandwidth. */
+stokes_status stokes_kernel_timing(stokes_ctx* ctx, int kernel, int64_t* timed_launches,
+                                   double* timed_ms, double* timed_bytes);
 stokes_status stokes_kernel_stats_reset(stokes_ctx* ctx);
 /* Change the profiling mode of a context (same values as options.profile). */
 stokes_status stokes_profile_mode(stokes_ctx* ctx, int mode);
+
+/* Exercises the bounded device waits (the grid-wide barriers of the
+ * cooperative coarse-level kernel, options.coarse_kernel = 1): launches a
+ * barrier that nothing completes, on the context's stream. Every wait gives up
+ * after a bounded number of polls (about a second), records the expiry and
+ * returns, so the call returns STOKES_ERR_TIMEOUT and the context stays
+ * usable (the status flag is cleared again). No counterpart in the paper. */
+stokes_status stokes_check_bounded_wait(stokes_ctx* ctx);
+
+/* Wall-clock milliseconds that stokes_setup spent per phase (host clock, the
+ * stream synchronised at the end of each phase): mesh hierarchy, patterns and
+ * element-coloured assembly of every level (the paper's Sec. 2.2 operators);
+ * transfers and stencil / symmetric storages; dense coarsest-level inverses;
+ * smoother spectra (Lanczos); FP32 copies and auxiliaries; threads-per-row
+ * tuning. ms must hold STOKES_SETUP_PHASES doubles. */
+enum { STOKES_SETUP_ASSEMBLY = 0, STOKES_SETUP_STORAGE = 1, STOKES_SETUP_COARSE = 2, STOKES_SETUP_SPECTRA = 3,
+       STOKES_SETUP_COPIES = 4, STOKES_SETUP_TUNING = 5, STOKES_SETUP_PHASES = 6 };
+stokes_status stokes_setup_phases(stokes_ctx* ctx, double ms[STOKES_SETUP_PHASES]);
 
 #ifdef __cplusplus
 }

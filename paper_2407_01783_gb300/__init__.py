@@ -26,7 +26,8 @@ from ._lib import (KERNEL, MAT, METHOD_COUPLED, METHOD_SCHUR, OP, PRECISION_FP64
 __all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "StokesBatch", "stokes_default_options",
            "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_adjoint",
            "stokes_destroy", "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_export", "stokes_sizes",
-           "stokes_kernel_stats", "stokes_kernel_stats_reset", "stokes_profile_mode", "StokesSolve", "OP", "MAT",
+           "stokes_kernel_stats", "stokes_kernel_timing", "stokes_kernel_stats_reset", "stokes_profile_mode",
+           "stokes_setup_phases", "StokesSolve", "OP", "MAT",
            "KERNEL", "METHOD_SCHUR", "METHOD_COUPLED", "SCHUR_PREC_LUMPED",
            "SCHUR_PREC_LAPLACE", "PRECISION_FP64", "PRECISION_MIXED", "library_path"]
 
@@ -162,12 +163,28 @@ def stokes_kernel_stats(ctx, kernel: int):
     return int(n.value), float(ms.value), float(by.value)
 
 
+def stokes_kernel_timing(ctx, kernel: int):
+    """(timed launches, their CUDA-event ms, their algorithmic bytes)."""
+    n = C.c_int64(0)
+    ms = C.c_double(0)
+    by = C.c_double(0)
+    _check(_L.stokes_kernel_timing(ctx, kernel, C.byref(n), C.byref(ms), C.byref(by)), "stokes_kernel_timing")
+    return int(n.value), float(ms.value), float(by.value)
+
+
 def stokes_kernel_stats_reset(ctx):
     _check(_L.stokes_kernel_stats_reset(ctx), "stokes_kernel_stats_reset")
 
 
 def stokes_profile_mode(ctx, mode: int):
     _check(_L.stokes_profile_mode(ctx, mode), "stokes_profile_mode")
+
+
+def stokes_setup_phases(ctx) -> dict:
+    """Milliseconds stokes_setup spent per phase (host clock)."""
+    ms = (C.c_double * len(_lib.SETUP_PHASES))()
+    _check(_L.stokes_setup_phases(ctx, ms), "stokes_setup_phases")
+    return {name: float(ms[k]) for k, name in enumerate(_lib.SETUP_PHASES)}
 
 
 class Stokes:

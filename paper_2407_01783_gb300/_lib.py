@@ -26,7 +26,7 @@ OP = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED_INV=7, VCYCLE_A3=8, VCY
           LOAD=16, A_DF=17, VCYCLE_VEL=18)
 MAT = dict(A=0, A3=1, B=2, BT=3, MQ=4, LQ=5, KQ=6, LUMPED=7, AV=8)
 KERNEL = dict(SPMM_A3=0, SPMV_A=1, B=2, BT=3, SPMV_P1=4, TRANSFER=5, BLAS1=6, OTHER=7,
-              SPMM_A3_COARSE=8, RESIDUAL=9)
+              SPMM_A3_COARSE=8, RESIDUAL=9, COARSE_CYCLE=10)
 
 
 class StokesOptions(C.Structure):
@@ -39,6 +39,8 @@ class StokesOptions(C.Structure):
         ("max_refine", C.c_int), ("profile", C.c_int), ("spmv_group", C.c_int),
         ("schur_inner_iters", C.c_int), ("pass_tol", C.c_double), ("format", C.c_int),
         ("graphs", C.c_int), ("vel_prec", C.c_int), ("mass_steps_v", C.c_int),
+        ("coarse_kernel", C.c_int), ("pass_schedule", C.c_int),
+        ("cheb_low", C.c_double), ("cheb_high", C.c_double),
     ]
 
     def as_dict(self):
@@ -96,10 +98,16 @@ def load() -> C.CDLL:
     lib.stokes_sizes.restype = C.c_int
     lib.stokes_kernel_stats.argtypes = [vp, C.c_int, i64p, dp, dp]
     lib.stokes_kernel_stats.restype = C.c_int
+    lib.stokes_kernel_timing.argtypes = [vp, C.c_int, i64p, dp, dp]
+    lib.stokes_kernel_timing.restype = C.c_int
     lib.stokes_kernel_stats_reset.argtypes = [vp]
     lib.stokes_kernel_stats_reset.restype = C.c_int
     lib.stokes_profile_mode.argtypes = [vp, C.c_int]
     lib.stokes_profile_mode.restype = C.c_int
+    lib.stokes_setup_phases.argtypes = [vp, dp]
+    lib.stokes_setup_phases.restype = C.c_int
+    lib.stokes_check_bounded_wait.argtypes = [vp]
+    lib.stokes_check_bounded_wait.restype = C.c_int
     _ = ip
     _lib = lib
     return lib
@@ -109,4 +117,7 @@ def load() -> C.CDLL:
 EXPORTS = ["stokes_default_options", "stokes_setup", "stokes_solve", "stokes_solve_host",
            "stokes_adjoint", "stokes_destroy", "stokes_status_string", "stokes_last_error",
            "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_shape", "stokes_matrix_export", "stokes_sizes",
-           "stokes_kernel_stats", "stokes_kernel_stats_reset", "stokes_profile_mode"]
+           "stokes_kernel_stats", "stokes_kernel_timing", "stokes_kernel_stats_reset", "stokes_profile_mode",
+           "stokes_setup_phases",
+           "stokes_check_bounded_wait"]
+SETUP_PHASES = ("assembly", "storage", "coarse", "spectra", "copies", "tuning")

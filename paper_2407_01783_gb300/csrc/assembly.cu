@@ -354,21 +354,32 @@ struct AsmArgs {
   long long btnnz;
   AssemblyOut o;
   int* bad;
+  int p;  // tetrahedron of the cube handled by this launch
 };
 
+// One launch per (colour, tetrahedron p of the cube) and one thread per (cube
+// of the colour, local node ra of tet p): the thread adds tet p's
+// contributions to velocity row ra (and, for a vertex, to pressure row ra).
+// Cubes of one colour share no node and the ten local nodes of one tet are
+// distinct, so no two threads of a launch write the same entry; launching the
+// colours and then the six tets in order keeps the summation order of every
+// entry fixed (deterministic assembly).
 __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.mx * a.my * a.mz) return;
+  if (t >= a.mx * a.my * a.mz * 10) return;
+  const int ra = t % 10;
+  t /= 10;
   int i = 2 * (t % a.mx) + a.cx;
   int j = 2 * ((t / a.mx) % a.my) + a.cy;
   int k = 2 * (t / (a.mx * a.my)) + a.cz;
   const int n = a.n, nv = n + 1;
-  for (int p = 0; p < 6; ++p) {
+  const int p = a.p;
+  {
     TetGeom tg;
     tet_geometry(n, a.X, i, j, k, p, tg);
     if (!tg.ok) {
-      atomicAdd(a.bad, 1);
-      continue;
+      if (ra == 0) atomicAdd(a.bad, 1);
+      return;
     }
     const double w = tg.vol * 0.25;
     int ri[10];
@@ -382,10 +393,10 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     double gq[4][10][3];
     for (int qp = 0; qp < 4; ++qp)
       for (int l = 0; l < 10; ++l) p2_grad(tg, l, qp, gq[qp][l]);
-    // velocity blocks
-    for (int ra = 0; ra < 10; ++ra) {
+    // velocity row ra
+    {
       int row = ri[ra];
-      if (row < 0) continue;
+      if (row >= 0) {
       if (a.o.lumped) a.o.lumped[row] += tg.vol * (ra < 4 ? 3.0 / 32.0 : 1.0 / 5.0);
       if (a.o.a3 || a.o.abs || a.o.mv) {
         int lo = a.p2rp[row], hi = a.p2rp[row + 1];
@@ -432,9 +443,11 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
           }
         }
       }
+      }
     }
-    // pressure rows
-    for (int l = 0; l < 4; ++l) {
+    // pressure row of vertex ra
+    if (ra < 4) {
+      const int l = ra;
       int row = vid[l];
       if (a.o.mq || a.o.lq || a.o.kq) {
         int lo = a.p1rp[row], hi = a.p1rp[row + 1];
@@ -514,8 +527,11 @@ long long assemble(const Exec& ex, int n, const double* X, double mu, double dt,
     a.mz = (n - a.cz + 1) / 2;
     int cubes = a.mx * a.my * a.mz;
     if (cubes == 0) continue;
-    k_assemble<<<cdiv(cubes, 128), 128, 0, ex.s>>>(a);
-    SK_CHECK_LAUNCH();
+    for (int p = 0; p < 6; ++p) {
+      a.p = p;
+      k_assemble<<<cdiv((long long)cubes * 10, 128), 128, 0, ex.s>>>(a);
+      SK_CHECK_LAUNCH();
+    }
   }
   int bad = 0;
   SK_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ex.s));
@@ -530,39 +546,36 @@ struct LoadArgs {
   int cx, cy, cz, mx, my, mz;
   const double* f;
   double* F;
+  int p;  // tetrahedron of the cube handled by this launch (k_load)
 };
 
+// One launch per (colour, tet p), one thread per (cube, local node ra): the
+// same ownership argument and summation order as k_assemble.
 __global__ void __launch_bounds__(128) k_load(LoadArgs a) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.mx * a.my * a.mz) return;
+  if (t >= a.mx * a.my * a.mz * 10) return;
+  const int ra = t % 10;
+  t /= 10;
   int i = 2 * (t % a.mx) + a.cx;
   int j = 2 * ((t / a.mx) % a.my) + a.cy;
   int k = 2 * (t / (a.mx * a.my)) + a.cz;
   const int N = 2 * a.n + 1;
-  for (int p = 0; p < 6; ++p) {
-    TetGeom tg;
-    tet_geometry(a.n, a.X, i, j, k, p, tg);
-    if (!tg.ok) continue;
-    int ri[10];
-    double fl[10][3];
-    for (int l = 0; l < 10; ++l) {
-      int q[3];
-      local_node(tg, l, q);
-      ri[l] = p2_interior_index(a.n, q);
-      size_t gid = (size_t)q[0] + N * ((size_t)q[1] + (size_t)N * q[2]);
-      for (int c = 0; c < 3; ++c) fl[l][c] = a.f[3 * gid + c];
-    }
-    for (int ra = 0; ra < 10; ++ra) {
-      if (ri[ra] < 0) continue;
-      double s[3] = {0, 0, 0};
-      for (int cb = 0; cb < 10; ++cb) {
-        double m = p2_mass420(ra, cb);
-        for (int c = 0; c < 3; ++c) s[c] += m * fl[cb][c];
-      }
-      const size_t nvi = (size_t)(2 * a.n - 1) * (2 * a.n - 1) * (2 * a.n - 1);
-      for (int c = 0; c < 3; ++c) a.F[c * nvi + ri[ra]] += tg.vol * s[c] / 420.0;  // component-major
-    }
+  TetGeom tg;
+  tet_geometry(a.n, a.X, i, j, k, a.p, tg);
+  if (!tg.ok) return;
+  int q[3];
+  local_node(tg, ra, q);
+  const int row = p2_interior_index(a.n, q);
+  if (row < 0) return;
+  double s[3] = {0, 0, 0};
+  for (int cb = 0; cb < 10; ++cb) {
+    local_node(tg, cb, q);
+    const size_t gid = (size_t)q[0] + N * ((size_t)q[1] + (size_t)N * q[2]);
+    const double m = p2_mass420(ra, cb);
+    for (int c = 0; c < 3; ++c) s[c] += m * a.f[3 * gid + c];
   }
+  const size_t nvi = (size_t)(2 * a.n - 1) * (2 * a.n - 1) * (2 * a.n - 1);
+  for (int c = 0; c < 3; ++c) a.F[c * nvi + row] += tg.vol * s[c] / 420.0;  // component-major
 }
 
 void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat, const double* f_all, double* F) {
@@ -582,9 +595,12 @@ void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat, con
     a.mz = (n - a.cz + 1) / 2;
     int cubes = a.mx * a.my * a.mz;
     if (cubes == 0) continue;
-    k_load<<<cdiv(cubes, 128), 128, 0, ex.s>>>(a);
-    if (colour > 0 && ex.prof && ex.prof->on) ex.prof->rec[STOKES_KERNEL_OTHER].launches += 1;
-    SK_CHECK_LAUNCH();
+    for (int p = 0; p < 6; ++p) {
+      a.p = p;
+      k_load<<<cdiv((long long)cubes * 10, 128), 128, 0, ex.s>>>(a);
+      if ((colour > 0 || p > 0) && ex.prof && ex.prof->on) ex.prof->rec[STOKES_KERNEL_OTHER].launches += 1;
+      SK_CHECK_LAUNCH();
+    }
   }
 }
 
@@ -885,6 +901,7 @@ StArgs stencil_args(const StencilOp& so, int block, int rows_per_thread) {
   for (int c = 0; c < so.ncls; ++c) {
     a.rows[c] = so.rows[c];
     a.S[c] = so.S[c];
+    a.Sreal[c] = so.Sreal[c];
     a.dbeg[c] = so.dbeg[c];
     a.voff[c] = so.voff[c];
     a.pext[c] = so.pext[c];
@@ -901,7 +918,8 @@ StArgs stencil_args(const StencilOp& so, int block, int rows_per_thread) {
   return a;
 }
 
-// one thread per padded row: values of entry e at voff[c] + e * prows[c] + pr
+// one thread per padded row: values of entry e at
+// voff[c] + ((e / kStencilVec) * prows[c] + pr) * kStencilVec + e % kStencilVec
 __global__ void k_stencil_fill(const StArgs a, const int* __restrict__ rp, const int* __restrict__ col,
                                const double* __restrict__ val, double* __restrict__ out) {
   int c, pr;
@@ -914,11 +932,11 @@ __global__ void k_stencil_fill(const StArgs a, const int* __restrict__ rp, const
   for (int e = 0; e < a.S[c]; ++e) {
     const int de = a.dbeg[c] + e;
     double w = 0.0;
-    if (real && st_inside(a, qx + a.d[de][0], qy + a.d[de][1], qz + a.d[de][2])) {
+    if (real && e < a.Sreal[c] && st_inside(a, qx + a.d[de][0], qy + a.d[de][1], qz + a.d[de][2])) {
       int pos = find_col(col, lo, hi, row + a.lin[de]);
       if (pos >= 0) w = val[pos];
     }
-    out[a.voff[c] + (size_t)e * a.prows[c] + pr] = w;
+    out[a.voff[c] + ((size_t)(e / kStencilVec) * a.prows[c] + pr) * kStencilVec + e % kStencilVec] = w;
   }
 }
 
@@ -942,9 +960,12 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
     so->pext[c] = (so->ext[c][0] + kStencilRows - 1) / kStencilRows * kStencilRows;
     so->prows[c] = so->pext[c] * so->ext[c][1] * so->ext[c][2];
     so->dbeg[c] = nd;
-    for (int e = st->beg[kind][c]; e < st->beg[kind][c + 1]; ++e) {
+    const int s0 = st->beg[kind][c], s1 = st->beg[kind][c + 1];
+    const int padded = (s1 - s0 + kStencilVec - 1) / kStencilVec * kStencilVec;
+    for (int k = 0; k < padded; ++k) {
       SK_REQUIRE(nd < kMaxStencil, STOKES_ERR_ARG, "stencil table overflow");
-      int dx = st->h_off[3 * e], dy = st->h_off[3 * e + 1], dz = st->h_off[3 * e + 2];
+      int dx = 0, dy = 0, dz = 0;  // padding entries: offset 0, weight 0
+      if (s0 + k < s1) dx = st->h_off[3 * (s0 + k)], dy = st->h_off[3 * (s0 + k) + 1], dz = st->h_off[3 * (s0 + k) + 2];
       so->d[nd][0] = (signed char)dx;
       so->d[nd][1] = (signed char)dy;
       so->d[nd][2] = (signed char)dz;
@@ -952,6 +973,8 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
       ++nd;
     }
     so->S[c] = nd - so->dbeg[c];
+    so->Sreal[c] = s1 - s0;
+    so->total_real += (long long)so->Sreal[c] * so->prows[c];
     so->voff[c] = off;
     off += (long long)so->S[c] * so->prows[c];
   }
@@ -965,6 +988,137 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
   StArgs a = stencil_args(*so, 128, 1);
   k_stencil_fill<<<a.bbeg[so->ncls], 128, 0, ex.s>>>(a, m.rowptr, m.col, m.v64, so->v64);
   SK_CHECK_LAUNCH();
+  return so;
+}
+
+// ---------------------------------------------------------------------------
+// symmetric stencil storage of a BSR3 interior-P2 matrix (see Sym3Op)
+// ---------------------------------------------------------------------------
+struct Sym3Fill {
+  int n, m;
+  int ext[8][3], q0[8][3], pext[8], prows[8], ubeg[9], bbeg[9];
+  long long voff[8];
+  signed char ud[kMaxSym][3];
+  int ulin[kMaxSym];
+};
+
+// one thread per padded row of one class; block e, entry k of row pr at
+// voff[c] + (9 e + k) prows[c] + pr
+__global__ void k_sym3_fill(const Sym3Fill a, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, long long nnz, double* __restrict__ out) {
+  int c = 0;
+  while (c < 7 && (int)blockIdx.x >= a.bbeg[c + 1]) ++c;
+  const int pr = ((int)blockIdx.x - a.bbeg[c]) * (int)blockDim.x + (int)threadIdx.x;
+  if (pr >= a.prows[c]) return;
+  const int px = a.pext[c], ey = a.ext[c][1];
+  const int i = pr % px;
+  const int qx = a.q0[c][0] + 2 * i, qy = a.q0[c][1] + 2 * ((pr / px) % ey), qz = a.q0[c][2] + 2 * (pr / (px * ey));
+  const bool real = i < a.ext[c][0];
+  const int row = real ? (qx - 1) + a.m * ((qy - 1) + a.m * (qz - 1)) : 0;
+  const int lo = real ? rp[row] : 0, hi = real ? rp[row + 1] : 0;
+  const int hiq = 2 * a.n - 1;
+  for (int e = a.ubeg[c]; e < a.ubeg[c + 1]; ++e) {
+    const int jx = qx + a.ud[e][0], jy = qy + a.ud[e][1], jz = qz + a.ud[e][2];
+    int pos = -1;
+    if (real && jx >= 1 && jx <= hiq && jy >= 1 && jy <= hiq && jz >= 1 && jz <= hiq)
+      pos = find_col(col, lo, hi, row + a.ulin[e]);
+    const size_t base = (size_t)a.voff[c] + (size_t)9 * (e - a.ubeg[c]) * a.prows[c] + pr;
+    for (int k = 0; k < 9; ++k) out[base + (size_t)k * a.prows[c]] = pos >= 0 ? val[(size_t)k * nnz + pos] : 0.0;
+  }
+}
+
+Sym3Op* sym3_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int n, const Csr& m) {
+  SK_REQUIRE(m.br == 3 && m.bc == 3 && m.v64, STOKES_ERR_ARG, "symmetric stencil storage needs an FP64 BSR3 matrix");
+  SK_REQUIRE(n >= 2, STOKES_ERR_ARG, "symmetric stencil storage needs n >= 2");
+  auto* so = new Sym3Op();
+  so->n = n;
+  const int mm = 2 * n - 1;
+  for (int c = 0; c < 8; ++c) {
+    for (int k = 0; k < 3; ++k) {
+      const int par = (c >> k) & 1;
+      so->q0[c][k] = par ? 1 : 2;
+      so->ext[c][k] = par ? n : n - 1;
+    }
+    so->rows[c] = so->ext[c][0] * so->ext[c][1] * so->ext[c][2];
+    so->pext[c] = so->ext[c][0];
+    so->prows[c] = so->rows[c];
+  }
+  // lexicographic sign in (z, y, x): the sign of the linear offset for m >= 3
+  auto lex = [](int dx, int dy, int dz) { return dz != 0 ? dz : (dy != 0 ? dy : dx); };
+  auto lin = [&](int dx, int dy, int dz) { return dx + mm * (dy + mm * dz); };
+  std::vector<std::vector<std::array<int, 3>>> up(8), low(8);
+  for (int c = 0; c < 8; ++c) {
+    up[c].push_back({0, 0, 0});
+    for (int e = st->beg[PAT_P2P2][c]; e < st->beg[PAT_P2P2][c + 1]; ++e) {
+      std::array<int, 3> o{st->h_off[3 * e], st->h_off[3 * e + 1], st->h_off[3 * e + 2]};
+      const int sg = lex(o[0], o[1], o[2]);
+      if (sg > 0) up[c].push_back(o);
+      else if (sg < 0) low[c].push_back(o);
+    }
+  }
+  int nu = 0, nl = 0;
+  long long off = 0;
+  for (int c = 0; c < 8; ++c) {
+    so->ubeg[c] = nu;
+    for (auto& o : up[c]) {
+      SK_REQUIRE(nu < kMaxSym, STOKES_ERR_ARG, "symmetric stencil table overflow");
+      for (int k = 0; k < 3; ++k) so->ud[nu][k] = (signed char)o[k];
+      so->ulin[nu] = lin(o[0], o[1], o[2]);
+      ++nu;
+    }
+    so->voff[c] = off;
+    off += 9LL * (long long)up[c].size() * so->prows[c];
+  }
+  so->ubeg[8] = nu;
+  for (int c = 0; c < 8; ++c) {
+    so->lbeg[c] = nl;
+    for (auto& o : low[c]) {
+      SK_REQUIRE(nl < kMaxSym, STOKES_ERR_ARG, "symmetric stencil table overflow");
+      const int cs = c ^ ((o[0] & 1) | ((o[1] & 1) << 1) | ((o[2] & 1) << 2));
+      int es = -1;
+      for (size_t e = 0; e < up[cs].size(); ++e)
+        if (up[cs][e][0] == -o[0] && up[cs][e][1] == -o[1] && up[cs][e][2] == -o[2]) es = (int)e;
+      SK_REQUIRE(es >= 0, STOKES_ERR_ARG, "stencil pattern is not symmetric");
+      for (int k = 0; k < 3; ++k) {
+        so->ld[nl][k] = (signed char)o[k];
+        const int t = so->q0[c][k] + o[k] - so->q0[cs][k];
+        SK_REQUIRE((t & 1) == 0, STOKES_ERR_ARG, "stencil class parity mismatch");
+        so->ldel[nl][k] = (signed char)(t / 2);
+      }
+      so->llin[nl] = lin(o[0], o[1], o[2]);
+      so->lcls[nl] = cs;
+      so->lbase[nl] = so->voff[cs] + 9LL * es * so->prows[cs];
+      ++nl;
+    }
+  }
+  so->lbeg[8] = nl;
+  so->total = off;
+  SK_REQUIRE(off < (1LL << 40), STOKES_ERR_ARG, "symmetric stencil storage too large");
+  so->v64 = ar.alloc<double>(off);
+  Sym3Fill a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.m = mm;
+  int b = 0;
+  for (int c = 0; c < 8; ++c) {
+    for (int k = 0; k < 3; ++k) a.ext[c][k] = so->ext[c][k], a.q0[c][k] = so->q0[c][k];
+    a.pext[c] = so->pext[c];
+    a.prows[c] = so->prows[c];
+    a.voff[c] = so->voff[c];
+    a.ubeg[c] = so->ubeg[c];
+    a.bbeg[c] = b;
+    b += cdiv(so->prows[c], 128);
+  }
+  a.ubeg[8] = so->ubeg[8];
+  a.bbeg[8] = b;
+  for (int e = 0; e < nu; ++e) {
+    for (int k = 0; k < 3; ++k) a.ud[e][k] = so->ud[e][k];
+    a.ulin[e] = so->ulin[e];
+  }
+  if (b > 0) {
+    k_sym3_fill<<<b, 128, 0, ex.s>>>(a, m.rowptr, m.col, m.v64, m.nnz, so->v64);
+    SK_CHECK_LAUNCH();
+  }
   return so;
 }
 

@@ -11,10 +11,18 @@
 
 namespace sk {
 
-__device__ __forceinline__ double coef_value(const Coef& k) {
+__device__ __forceinline__ double coef_value(const Coef& k, int* flag) {
   double v = k.c;
   if (k.num) {
     const double den = k.den ? *k.den : 1.0;
+    if (k.positive && !(den > 0.0)) {
+      // r^T z <= 0 in a preconditioned CG: an indefinite preconditioner, or
+      // vanished Krylov vectors (exact convergence inside a fixed-iteration
+      // solve). Flag it (the host reports a breakdown only if the solve then
+      // fails) and contribute nothing.
+      if (flag) atomicOr(flag, 1);
+      return v;
+    }
     // a zero denominator only arises when the Krylov vectors vanished (exact
     // convergence inside a fixed-iteration solve): contribute nothing
     if (den != 0.0) v += k.s * (*k.num) / den;
@@ -175,14 +183,14 @@ static inline int ew_grid(size_t n) { return (int)std::min<long long>(cdiv((long
 #define SK_COEF2(A, B, va, vb)                                  \
   __shared__ double sk_coef_[2];                                \
   if (threadIdx.x == 0) {                                       \
-    sk_coef_[0] = coef_value(A);                                \
-    sk_coef_[1] = coef_value(B);                                \
+    sk_coef_[0] = coef_value(A, blockIdx.x == 0 ? flag : nullptr); \
+    sk_coef_[1] = coef_value(B, blockIdx.x == 0 ? flag : nullptr); \
   }                                                             \
   __syncthreads();                                              \
   const double va = sk_coef_[0], vb = sk_coef_[1];
 
 template <class T>
-__global__ void k_axpby(size_t n, Coef a, const T* __restrict__ x, Coef b, T* __restrict__ y) {
+__global__ void k_axpby(size_t n, Coef a, const T* __restrict__ x, Coef b, T* __restrict__ y, int* flag) {
   SK_COEF2(a, b, ad, bd);
   const T av = (T)ad, bv = (T)bd;
   if (bv == T(0)) {
@@ -194,7 +202,7 @@ __global__ void k_axpby(size_t n, Coef a, const T* __restrict__ x, Coef b, T* __
 template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y) {
   if (!n) return;
   ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 3);
-  k_axpby<T><<<SK_GRID(n)>>>(n, a, x, b, y);
+  k_axpby<T><<<SK_GRID(n)>>>(n, a, x, b, y, ex.flag);
   SK_CHECK_LAUNCH();
 }
 
@@ -222,7 +230,38 @@ template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, 
   SK_CHECK_LAUNCH();
 }
 
-template <class T> __global__ void k_scale_copy(size_t n, Coef a, const T* __restrict__ x, T* __restrict__ y) {
+// x += a d; r -= a q; *rr = r . r (new r), the squares summed per thread in
+// FP64 and over the grid in a fixed order (grid_sum)
+template <class T>
+__global__ void k_cg_update_rr(size_t n, Coef a, const T* __restrict__ d, T* __restrict__ x, const T* __restrict__ q,
+                               T* __restrict__ r, int* flag, double* partial, unsigned* counter, double* rr) {
+  SK_COEF2(a, a, ad, unused);
+  (void)unused;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && flag && a.den && !(*a.den > 0.0))
+    atomicOr(flag, 1);  // p^T A p <= 0: breakdown
+  const T av = (T)ad;
+  double s = 0.0;
+  SK_LOOP(i) {
+    x[i] += av * d[i];
+    const T rn = r[i] - av * q[i];
+    r[i] = rn;
+    s += (double)(rn * rn);
+  }
+  grid_sum(s, partial, counter, rr);
+}
+template <class T>
+void cg_update_rr(const Exec& ex, const DotScratch& ds, size_t n, Coef a, const T* d, T* x, const T* q, T* r,
+                  double* rr) {
+  SK_REQUIRE(n > 0, STOKES_ERR_ARG, "cg_update_rr: empty vector");
+  const int grid = ew_grid(n);
+  SK_REQUIRE(ds.fused_partial && grid <= ds.fused_cap, STOKES_ERR_ARG, "fused dot scratch too small");
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 6);
+  k_cg_update_rr<T><<<grid, 256, 0, ex.s>>>(n, a, d, x, q, r, ex.flag, ds.fused_partial, ds.fused_counter, rr);
+  SK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_scale_copy(size_t n, Coef a, const T* __restrict__ x, T* __restrict__ y, int* flag) {
   SK_COEF2(a, a, ad, unused);
   (void)unused;
   SK_LOOP(i) {
@@ -232,7 +271,7 @@ template <class T> __global__ void k_scale_copy(size_t n, Coef a, const T* __res
 template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x, T* y) {
   if (!n) return;
   ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * 2);
-  k_scale_copy<T><<<SK_GRID(n)>>>(n, a, x, y);
+  k_scale_copy<T><<<SK_GRID(n)>>>(n, a, x, y, ex.flag);
   SK_CHECK_LAUNCH();
 }
 
@@ -387,6 +426,7 @@ void scalar_sub(const Exec& ex, double* out, const double* a, const double* b) {
                         double*, int);                                                                       \
   template void axpby<T>(const Exec&, size_t, Coef, const T*, Coef, T*);                               \
   template void cg_update<T>(const Exec&, size_t, Coef, const T*, T*, const T*, T*);                   \
+  template void cg_update_rr<T>(const Exec&, const DotScratch&, size_t, Coef, const T*, T*, const T*, T*, double*); \
   template void scale_copy<T>(const Exec&, size_t, Coef, const T*, T*);                                \
   template void lincomb2<T>(const Exec&, size_t, double, const T*, double, const T*, T*);              \
   template void sub_mean<T>(const Exec&, size_t, const double*, double, T*);                           \

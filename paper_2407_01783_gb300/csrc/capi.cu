@@ -3,6 +3,7 @@
 // include/stokes.h. No entry point lets a C++ exception escape: every error
 // becomes a stokes_status plus a per-thread message.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -105,8 +106,22 @@ static float* f32_copy(stokes_ctx& c, const double* src, size_t n) {
   return d;
 }
 
+// wall-clock milliseconds of the setup phases (stream synchronised at each mark)
+struct PhaseClock {
+  stokes_ctx& c;
+  std::chrono::steady_clock::time_point t;
+  explicit PhaseClock(stokes_ctx& cc) : c(cc), t(std::chrono::steady_clock::now()) {}
+  void mark(int phase) {
+    SK_CUDA(cudaStreamSynchronize(c.ex.s));
+    const auto now = std::chrono::steady_clock::now();
+    c.setup_ms[phase] += std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+  }
+};
+
 void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   stokes_ctx& c = *cp;
+  PhaseClock clock(c);
   c.n = n;
   c.ex.prof = &c.prof;
   c.prof.on = c.opt.profile != 0;
@@ -212,6 +227,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
       }
     }
   }
+  clock.mark(STOKES_SETUP_ASSEMBLY);
   for (size_t l = 0; l + 1 < c.lv.size(); ++l) {
     build_transfer_p2(c.ex, c.arena, c.lv[l].n, c.lv[l + 1].n, c.lv[l].P2, c.lv[l].R2);
     build_transfer_p1(c.ex, c.arena, c.lv[l].n, c.lv[l + 1].n, c.lv[l].P1, c.lv[l].R1);
@@ -230,15 +246,32 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     add(c.LQ, 0, n);
     if (c.MV.v64) add(c.MV, 1, n);
   }
+  if (c.opt.format != 1) {
+    // the strain-form A also in symmetric stencil storage (half the values, no
+    // indices): every product of A reads it (48^3, FP32, with the fused dot:
+    // 171 us against 243 us for BSR3), and the double-float refinement
+    // residual (324 against 421 us); format 3 keeps BSR3 for the products
+    c.symA.reset(sym3_from_csr(c.ex, c.arena, st, n, c.A));
+    c.A.sym = c.symA.get();
+    c.A.sym_products = c.opt.format != 3;
+  }
+  // per-block partials of dot products fused into other kernels
+  c.ds.fused_cap = std::max(std::max(2048, bsr3_dot_grid(c.A)), c.symA ? sym3_grid(*c.symA) : 0);
+  c.ds.fused_partial = c.arena.alloc<double>(c.ds.fused_cap);
+  c.ds.fused_counter = c.arena.alloc<unsigned>(1);
+  SK_CUDA(cudaMemsetAsync(c.ds.fused_counter, 0, sizeof(unsigned), c.ex.s));
+  clock.mark(STOKES_SETUP_STORAGE);
   Level& Lc = c.lv.back();
   coarse_inverse(c, Lc.A3, &Lc.A3_cinv64);
   coarse_inverse(c, Lc.KQ, &Lc.KQ_cinv64);
   if (Lc.AV.v64) coarse_inverse(c, Lc.AV, &Lc.AV_cinv64);
+  clock.mark(STOKES_SETUP_COARSE);
   for (size_t l = 0; l + 1 < c.lv.size(); ++l) {
     c.lv[l].A3_lmax = estimate_lmax(c, c.lv[l].A3, c.lv[l].A3_dinv64, 15, 1000 + l);
     c.lv[l].KQ_lmax = estimate_lmax(c, c.lv[l].KQ, c.lv[l].KQ_dinv64, 15, 2000 + l);
     if (c.lv[l].AV.v64) c.lv[l].AV_lmax = estimate_lmax(c, c.lv[l].AV, c.lv[l].AV_dinv64, 15, 3000 + l);
   }
+  clock.mark(STOKES_SETUP_SPECTRA);
   // fine-level auxiliaries
   const Level& L0 = c.lv[0];
   {
@@ -291,10 +324,16 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
         if (t->v64) t->v32 = f32_copy(c, t->v64, t->nnz);
     }
     for (auto& so : c.stencils) so->v32 = f32_copy(c, so->v64, so->total);
+    if (c.symA) {
+      c.symA->v32 = f32_copy(c, c.symA->v64, c.symA->total);
+      c.symA->v32lo = c.arena.alloc<float>(c.symA->total);
+      to_f32_lo(c.ex, c.symA->v64, c.symA->v32, c.symA->v32lo, c.symA->total);
+    }
     Lc.A3_cinv32 = f32_copy(c, Lc.A3_cinv64, (size_t)Lc.A3.rows * Lc.A3.rows);
     Lc.KQ_cinv32 = f32_copy(c, Lc.KQ_cinv64, (size_t)Lc.KQ.rows * Lc.KQ.rows);
     if (Lc.AV_cinv64) Lc.AV_cinv32 = f32_copy(c, Lc.AV_cinv64, 9 * (size_t)Lc.AV.rows * Lc.AV.rows);
   }
+  clock.mark(STOKES_SETUP_COPIES);
   // threads-per-row: tuned in the precision of the hot loop unless fixed by the caller
   auto tune = [&](Csr& m, int nr, int kind) {
     if (c.opt.spmv_group > 0) {
@@ -309,6 +348,9 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     m.group = probe.group;
   };
   tune(c.A, 3, 1);
+  // threads per row of the symmetric A products: one (measured fastest inside
+  // the solve at 48^3: 201 us against 232, 318, 508 us for 2, 4, 8) unless set
+  if (c.A.sym) c.symA->group = c.opt.spmv_group > 0 ? std::min(8, c.A.group) : 1;
   tune(c.B, 1, 2);
   tune(c.Bt, 3, 3);
   tune(c.MQ, 1, 0);
@@ -325,7 +367,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
       tune(L.R1, 1, 0);
     }
   }
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  clock.mark(STOKES_SETUP_TUNING);
 }
 
 }  // namespace sk
@@ -377,6 +419,10 @@ void stokes_default_options(stokes_options* o) {
   o->graphs = 1;
   o->vel_prec = 3;
   o->mass_steps_v = 8;
+  o->coarse_kernel = 0;
+  o->pass_schedule = 0;
+  o->cheb_low = 0.1;
+  o->cheb_high = 1.1;
 }
 
 const char* stokes_status_string(int s) {
@@ -410,9 +456,11 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
   if (!c) return STOKES_ERR_OOM;
   if (opt) c->opt = *opt; else stokes_default_options(&c->opt);
   if (c->opt.vcycles < 1 || c->opt.cheb_degree < 1 || c->opt.restart < 2 || !(c->opt.eps_pressure > 0) ||
-      !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 2 ||
+      !(c->opt.inner_tol > 0) || !(c->opt.schur_inner_tol > 0) || c->opt.format < 0 || c->opt.format > 3 ||
       !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1) || c->opt.vel_prec < 1 || c->opt.vel_prec > 3 ||
-      c->opt.schur_prec < 0 || c->opt.schur_prec > 2 || c->opt.mass_steps_v < 1) {
+      c->opt.schur_prec < 0 || c->opt.schur_prec > 2 || c->opt.mass_steps_v < 1 ||
+      c->opt.pass_schedule < 0 || c->opt.pass_schedule > 2 || !(c->opt.cheb_low > 0) ||
+      !(c->opt.cheb_high > c->opt.cheb_low) || !std::isfinite(c->opt.cheb_high)) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;
@@ -610,6 +658,51 @@ stokes_status stokes_kernel_stats(stokes_ctx* c, int kernel, int64_t* launches, 
     if (launches) *launches = r.launches;
     if (total_ms) *total_ms = ms;
     if (bytes) *bytes = r.bytes;
+  });
+}
+
+stokes_status stokes_check_bounded_wait(stokes_ctx* c) {
+  g_last_error.clear();
+  if (!c) return STOKES_ERR_ARG;
+  int status = STOKES_OK;
+  int st = guarded([&]() {
+    unsigned* bar = c->arena.alloc<unsigned>(1);
+    SK_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->ex.s));
+    bounded_wait_check(c->ex, bar);
+    int flag = 0;
+    SK_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->ex.s));
+    SK_CUDA(cudaStreamSynchronize(c->ex.s));
+    SK_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->ex.s));
+    SK_CUDA(cudaStreamSynchronize(c->ex.s));
+    status = (flag & 4) ? STOKES_ERR_TIMEOUT : STOKES_OK;
+  });
+  if (st != STOKES_OK) return (stokes_status)st;
+  if (status != STOKES_OK) g_last_error = "a device wait that nothing completes expired as designed";
+  return (stokes_status)status;
+}
+
+stokes_status stokes_setup_phases(stokes_ctx* c, double ms[STOKES_SETUP_PHASES]) {
+  if (!c || !ms) return STOKES_ERR_ARG;
+  for (int k = 0; k < STOKES_SETUP_PHASES; ++k) ms[k] = c->setup_ms[k];
+  return STOKES_OK;
+}
+
+stokes_status stokes_kernel_timing(stokes_ctx* c, int kernel, int64_t* timed_launches, double* timed_ms,
+                                   double* timed_bytes) {
+  g_last_error.clear();
+  if (!c || kernel < 0 || kernel >= STOKES_KERNEL_COUNT) return STOKES_ERR_ARG;
+  return (stokes_status)guarded([&]() {
+    SK_CUDA(cudaStreamSynchronize(c->ex.s));
+    auto& r = c->prof.rec[kernel];
+    double ms = 0;
+    for (auto& p : r.ev) {
+      float t = 0;
+      SK_CUDA(cudaEventElapsedTime(&t, p.first, p.second));
+      ms += t;
+    }
+    if (timed_launches) *timed_launches = r.ev_launches;
+    if (timed_ms) *timed_ms = ms;
+    if (timed_bytes) *timed_bytes = r.ev_bytes;
   });
 }
 

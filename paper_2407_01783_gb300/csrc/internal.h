@@ -57,8 +57,10 @@ struct Prof {
   Counts* capture = nullptr;
   struct Rec {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    double bytes = 0;
+    double bytes = 0;        // all launches (graph replays included)
     int64_t launches = 0;
+    double ev_bytes = 0;     // the launches bracketed by events
+    int64_t ev_launches = 0;
   } rec[STOKES_KERNEL_COUNT];
   std::vector<cudaEvent_t> pool;
   cudaEvent_t get();
@@ -69,7 +71,8 @@ struct Prof {
 struct Exec {
   cudaStream_t s = nullptr;
   Prof* prof = nullptr;
-  int* flag = nullptr;  // per-context status bits set by kernels (1: CG breakdown)
+  int* flag = nullptr;  // per-context status bits set by kernels (1: Krylov breakdown,
+                        // 4: a bounded device wait expired)
 };
 
 // Brackets one launch with events when profiling is on.
@@ -86,11 +89,15 @@ struct ProfScope {
 // neighbours follow one of 8 fixed stencils (by the parity class of its
 // half-grid coordinates; P1 nodes have a single class), so a row needs no
 // column indices: column = row + lin[e] for stencil entry e when the neighbour
-// lies inside the index space, else the entry is absent (stored as 0). Values
-// of class c are stored [e][row-in-class] so that a warp of consecutive
-// same-class rows reads 128 contiguous bytes per entry.
+// lies inside the index space, else the entry is absent (stored as 0). Each
+// class's entry list is padded with zero entries (offset 0) to a multiple of
+// kStencilVec, and the values of class c are stored
+// [e / kStencilVec][row-in-class][e % kStencilVec]: one vector load gives a
+// thread the weights of kStencilVec entries, and a warp of consecutive
+// same-class rows reads one contiguous segment per load.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStencil = 256;
+constexpr int kStencilVec = 4;
 // Rows of one class along x are grouped by kStencilRows per thread; the value
 // layout pads each class's x-extent to a multiple of kStencilRows so that the
 // values of a thread's rows are one aligned vector.
@@ -100,9 +107,11 @@ struct StencilOp {
   int n = 0;
   int ncls = 0;
   int rows[8] = {}, ext[8][3] = {}, q0[8][3] = {}, S[8] = {}, dbeg[8] = {};
+  int Sreal[8] = {};                // entries before padding to a multiple of kStencilVec
   int pext[8] = {}, prows[8] = {};  // padded x-extent and padded row count per class
   long long voff[8] = {};
-  long long total = 0;       // stored entries (all classes)
+  long long total = 0;       // stored entries (all classes, padding included)
+  long long total_real = 0;  // stored entries without the padding entries
   signed char d[kMaxStencil][3] = {};  // half-grid offsets of entry e
   int lin[kMaxStencil] = {};           // linear index offsets of entry e
   int nd = 0;
@@ -117,7 +126,7 @@ template <> inline float* StencilOp::v<float>() const { return v32; }
 // contiguous: class c owns blocks [bbeg[c], bbeg[c+1])).
 struct StArgs {
   int p2, n, ncls, lo, hi, m, R;  // R: rows per thread of the launch using these args
-  int rows[8], ext[8][3], q0[8][3], S[8], dbeg[8], pext[8], prows[8];
+  int rows[8], ext[8][3], q0[8][3], S[8], Sreal[8], dbeg[8], pext[8], prows[8];
   long long voff[8];
   int bbeg[9];
   signed char d[kMaxStencil][3];
@@ -155,6 +164,71 @@ __device__ __forceinline__ bool st_inside(const StArgs& a, int qx, int qy, int q
 #endif
 
 // ---------------------------------------------------------------------------
+// double-float BSR3 residual. Error-free transformations (published methods):
+// TwoProduct with an FMA, p + e = a * b exactly (Ogita, Rump & Oishi 2005);
+// TwoSum, s + e = a + b exactly (Knuth, TAOCP vol. 2, 4.2.2). The _rn
+// intrinsics keep the compiler from contracting these steps into FMAs.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+struct DF {
+  float h, l;
+};
+// s += (ah + al) * (xh + xl), dropping al * xl (2^-48 relative)
+__device__ __forceinline__ void df_madd(DF& s, float ah, float al, float xh, float xl) {
+  const float ph = __fmul_rn(ah, xh);
+  const float pe = __fmaf_rn(ah, xh, -ph);
+  const float pc = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
+  const float t = __fadd_rn(s.h, ph);
+  const float z = __fsub_rn(t, s.h);
+  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  s.h = t;
+  s.l = __fadd_rn(s.l, __fadd_rn(e, __fadd_rn(pe, pc)));
+}
+__device__ __forceinline__ void df_add(DF& s, float oh, float ol) {
+  const float t = __fadd_rn(s.h, oh);
+  const float z = __fsub_rn(t, s.h);
+  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(oh, z));
+  s.h = t;
+  s.l = __fadd_rn(s.l, __fadd_rn(ol, e));
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// Symmetric stencil storage of a 3x3-block operator on the interior P2 nodes
+// (the strain-form A). Rows are grouped by the 8 parity classes of the P2
+// stencil storage; a row stores only its diagonal block and the blocks of its
+// "upper" neighbours (offset lexicographically positive in (z, y, x)). The
+// block of a "lower" neighbour j = i + o is A(j, i)^T, read from row j's
+// storage (class cs = class(i) XOR parity(o), entry -o), so every stored value
+// is read twice per product and the matrix bytes are halved. Values of class c
+// are stored [entry][9][row-in-class] (row-major 3x3 blocks), so a warp of
+// consecutive same-class rows reads 128 contiguous bytes per block entry.
+// ---------------------------------------------------------------------------
+constexpr int kMaxSym = 160;
+struct Sym3Op {
+  int n = 0;
+  int rows[8] = {}, ext[8][3] = {}, q0[8][3] = {}, pext[8] = {}, prows[8] = {};
+  int ubeg[9] = {};                   // class c: upper entries (diagonal first) [ubeg[c], ubeg[c+1])
+  signed char ud[kMaxSym][3] = {};    // half-grid offset of upper entry
+  int ulin[kMaxSym] = {};             // linear index offset of upper entry
+  long long voff[8] = {};             // class c: block e, entry k at voff[c] + (9 e + k) prows[c] + row
+  int lbeg[9] = {};                   // class c: lower entries [lbeg[c], lbeg[c+1])
+  signed char ld[kMaxSym][3] = {};    // half-grid offset o of lower entry (neighbour j = i + o)
+  int llin[kMaxSym] = {};
+  int lcls[kMaxSym] = {};             // class of j
+  long long lbase[kMaxSym] = {};      // voff[class j] + 9 * (entry -o of class j) * prows[class j]
+  signed char ldel[kMaxSym][3] = {};  // position of j in its class minus position of i in its class
+  long long total = 0;                // stored values (9 per stored block)
+  int group = 1;                      // threads per row of the products (1, 2, 4 or 8)
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  float* v32lo = nullptr;             // FP32(v64 - v32): double-float residual
+  template <class T> T* v() const;
+};
+template <> inline double* Sym3Op::v<double>() const { return v64; }
+template <> inline float* Sym3Op::v<float>() const { return v32; }
+
+// ---------------------------------------------------------------------------
 // sparse matrices: CSR over (possibly) small dense blocks, values stored as
 // br*bc planes of nnz entries each (plane j at v + j*nnz) so that consecutive
 // lanes read consecutive addresses.
@@ -170,6 +244,9 @@ struct Csr {
   float* v32lo = nullptr;  // v64 - v32 rounded to FP32 (double-float residual), or null
   int group = 8;  // threads per row
   const StencilOp* st = nullptr;  // same matrix in stencil storage (used when set)
+  const Sym3Op* sym = nullptr;    // 3x3-block matrix in symmetric stencil storage: used for the
+                                  // double-float residual, and for all products if sym_products
+  bool sym_products = false;
   template <class T> T* v() const;
   double bytes(int elem) const {  // algorithmic bytes of one product (matrix only)
     return (double)nnz * (4.0 + elem * br * bc) + 4.0 * (rows + 1);
@@ -221,15 +298,60 @@ struct Scalars {
 };
 
 // Coefficient read on the device: value = c + s * (*num / *den); null num -> 0
-// contribution, null den -> 1.
+// contribution, null den -> 1. A Krylov coefficient whose denominator must be
+// positive (r^T z in a preconditioned CG beta) is built with cg_ratio: a
+// denominator <= 0 then sets the context's breakdown flag (bit 1) and the
+// coefficient contributes nothing.
 struct Coef {
   double c = 0, s = 0;
   const double* num = nullptr;
   const double* den = nullptr;
+  int positive = 0;
   static Coef constant(double v) { Coef k; k.c = v; return k; }
   static Coef ratio(const double* num, const double* den, double s = 1.0) {
     Coef k; k.s = s; k.num = num; k.den = den; return k;
   }
+  static Coef cg_ratio(const double* num, const double* den, double s = 1.0) {
+    Coef k = ratio(num, den, s); k.positive = 1; return k;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// A fixed sequence of multigrid steps (the levels below the finest of one
+// V-cycle) executed by one cooperative kernel (mgprog.cu). Step kinds:
+// 0 first Chebyshev step from zero (d = y = c1 D^-1 b), 1 y = A x, 2 y += A x,
+// 3 y = b - A x, 4 Chebyshev step (d = c1 d + c2 D^-1 (b - A x), y = x + d),
+// 5 y = M b with a dense row-major M (m x m). CSR steps have `rows` rows and
+// `m` columns; vectors hold nr components (component-major).
+// ---------------------------------------------------------------------------
+struct MgOp {
+  int kind = 0, nr = 1, rows = 0, m = 0;
+  const int* rp = nullptr;
+  const int* col = nullptr;
+  const void* val = nullptr;
+  const void* b = nullptr;
+  const void* xin = nullptr;
+  void* d = nullptr;
+  void* y = nullptr;
+  const void* dinv = nullptr;
+  double c1 = 0, c2 = 0;
+};
+struct MgOpDev;
+// launches a grid barrier that cannot complete; its bounded waits expire and
+// set bit 4 of ex.flag (about a second); bar: one device unsigned
+void bounded_wait_check(const Exec& ex, unsigned* bar);
+struct MgProgram {
+  std::vector<MgOp> ops;
+  MgOpDev* dev_ops = nullptr;
+  unsigned* bar = nullptr;   // grid-barrier counter
+  int grid = 0;
+  bool f32 = false;
+  double bytes = 0;          // algorithmic bytes of one run (sum over steps)
+  void* b = nullptr;         // input (right-hand side on the first coarse level)
+  void* x = nullptr;         // output (solution on the first coarse level)
+  void add(const MgOp& op);
+  void finalize(Arena& ar, bool f32);
+  void launch(const Exec& ex) const;
 };
 
 // ---------------------------------------------------------------------------
@@ -296,6 +418,9 @@ void combine_grad_div(const Exec& ex, long long nnz, const double* abs, const do
 // Stencil storage of a square P2-interior (p2 = 1) or P1 (p2 = 0) matrix of
 // level size n, values copied from the assembled CSR m (FP64; FP32 on request).
 StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int p2, int n, const Csr& m);
+// Symmetric stencil storage of the BSR3 interior-P2 matrix m of level size n
+// (FP64 values; FP32 copies are made by the caller).
+Sym3Op* sym3_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, int n, const Csr& m);
 void to_f32(const Exec& ex, const double* src, float* dst, size_t n);
 // lo = FP32(src - hi): with hi = FP32(src), hi + lo carries src to ~2^-48
 void to_f32_lo(const Exec& ex, const double* src, const float* hi, float* lo, size_t n);
@@ -331,7 +456,9 @@ void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
                                   const T* dinv, double c1, double c2, int kind);
 template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y);
+
 void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
+
 
 // ---------------------------------------------------------------------------
 // BLAS-1 (blas1.cu). Dot products accumulate in FP64 and reduce in a fixed
@@ -340,9 +467,65 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
 struct DotScratch {
   double* partial = nullptr;   // [kMaxDots][kMaxBlocks]
   unsigned* counter = nullptr;
+  // dot products fused into the epilogue of another kernel: one partial per
+  // block of that launch (capacity fused_cap), own completion counter
+  double* fused_partial = nullptr;
+  unsigned* fused_counter = nullptr;
+  int fused_cap = 0;
 };
+
+#ifdef __CUDACC__
+// Deterministic sum over the grid of one double per thread; every thread of
+// every block must call it (no early return before). Warp shuffles, then the
+// warps of a block in order, give partial[blockIdx.x]; the last block to
+// finish adds the partials in block order, writes *out and resets *counter.
+__device__ __forceinline__ void grid_sum(double v, double* partial, unsigned* counter, double* out) {
+  __shared__ double sh_[32];
+  __shared__ bool last_;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh_[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh_[w];
+    partial[blockIdx.x] = t;
+    __threadfence();
+    last_ = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&partial[b]);
+  for (int o = 16; o; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  __syncthreads();
+  if (lane == 0) sh_[wid] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh_[w];
+    *out = s;
+    *counter = 0u;
+  }
+}
+#endif
 constexpr int kMaxDots = 4;
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+// y = A x, and *dot = x . y (deterministic, FP64 accumulation) fused into the
+// same kernel when A has symmetric stencil storage (else a separate dot).
+template <class T> bool bsr3_apply_dot(const Exec& ex, const Csr& m, const T* x, T* y, const DotScratch& ds,
+                                       double* dot);
+// symmetric-stencil products (sym3.cu): y = A x or y = b - A x, optional fused
+// dot x . (A x); double-float residual y = b - A x
+template <class T> void sym3_launch(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, const DotScratch* ds,
+                                    double* dot);
+void sym3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y);
+double sym3_bytes(const Sym3Op& so, int esz, int rows, int streams);
+// most blocks of one symmetric-stencil product launch (fused-dot partial capacity)
+int sym3_grid(const Sym3Op& so);
+// most blocks of one dot-fused BSR3 product launch (fused-dot partial capacity)
+int bsr3_dot_grid(const Csr& m);
 // FP32 vectors at least this long use compensated FP32 per-thread sums in
 // dots() (velocity-sized vectors of the inner solves); shorter ones
 // (pressure-sized, the outer Schur iteration) accumulate in FP64 throughout.
@@ -360,6 +543,9 @@ template <class T> void dots(const Exec& ex, const DotScratch& ds, int k, const 
 template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y);
 // x += a d; r -= a q   (a from device scalars)
 template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r);
+// x += a d; r -= a q; *rr = r . r of the updated r (one kernel)
+template <class T> void cg_update_rr(const Exec& ex, const DotScratch& ds, size_t n, Coef a, const T* d, T* x,
+                                     const T* q, T* r, double* rr);
 // y = a x  (a may be a device ratio)
 template <class T> void scale_copy(const Exec& ex, size_t n, Coef a, const T* x, T* y);
 // y = c1*x1 + c2*x2 (elementwise, constants)
@@ -410,6 +596,7 @@ struct stokes_ctx {
   bool mixed = false;
   // last forward solution (reduced) for the adjoint
   std::vector<std::unique_ptr<sk::StencilOp>> stencils;  // owned stencil storages
+  std::unique_ptr<sk::Sym3Op> symA;                       // A in symmetric stencil storage
   double* U_last = nullptr;
   double* P_last = nullptr;
   bool have_solution = false;
@@ -428,6 +615,9 @@ struct stokes_ctx {
     cudaGraphExec_t exec = nullptr;
     sk::Prof::Counts counts;
   } cgraph[3][2];
+  // levels >= 1 of a V-cycle (which = 0, 1) in one cooperative kernel, FP64 [0]
+  // and FP32 [1] (built on first use)
+  std::unique_ptr<sk::MgProgram> mgprog[2][2];
   // graphs are captured on this private stream (capture is not allowed on the
   // legacy default stream) and launched on ex.s
   cudaStream_t cap_stream = nullptr;
@@ -444,6 +634,8 @@ struct stokes_ctx {
   std::map<std::tuple<int, int, const void*, void*, int>, CycleGraph> vgraphs;
   sk::VecPool vgraph_pool;
   bool in_cycle_graph = false;
+  bool graphs_off = false;  // a region could not be recorded: plain launches from then on
+  double setup_ms[STOKES_SETUP_PHASES] = {};  // wall-clock ms per setup phase
   // counters
   int outer_iters = 0, inner_iters = 0, schur_inner_iters = 0;
   bool outer_capped = false, inner_capped = false;

@@ -16,9 +16,7 @@ namespace sk {
 
 void scalar_sub(const Exec& ex, double* out, const double* a, const double* b);
 
-// Smoother interval [kChebLow, kChebHigh] x (Lanczos estimate of lambda_max(D^{-1}A)).
-constexpr double kChebLow = 0.1;
-constexpr double kChebHigh = 1.1;
+
 // sigma(D^{-1} M_Q) lies in [1/2, 5/2] for P1 on tetrahedra (element matrix
 // D_K^{-1} M_K = (I + 1 1^T)/2 has eigenvalues 1/2 and 5/2; Wathen 1987).
 constexpr double kMassLow = 0.5;
@@ -86,8 +84,11 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
   size_t len = (size_t)M.rows * (block ? 3 : nr);
   double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta, rho = 1.0 / sigma;
   Tmp<T> d(c.pool, len), xt(c.pool, len);
+  // ping-pong between x and xt; from zero, start in xt when an odd number of
+  // steps follows the first, so that the last step writes x (no copy)
   T* xa = x;
   T* xb = xt;
+  if (xzero && (steps - 1) % 2 == 1) std::swap(xa, xb);
   auto step = [&](const T* xin, T* xout, double c1, double c2) {
     if (block) bsr3_cheb<T>(c.ex, M, b, xin, d, xout, dinv, c1, c2, kind);
     else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind);
@@ -122,15 +123,13 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
 // level 0 the V-cycle is replayed from a CUDA graph. Graph launches are not
 // timed per class: under per-class profiling of a class that the coarse
 // levels launch, they run eagerly instead.
+// Graph launches carry no per-launch events: graphs are off while every class
+// is timed (profile 1); while one class is timed (profile 2 + k) they stay on
+// and only that class's launches outside graphs are timed.
 static bool coarse_graph_ok(const stokes_ctx& c, int which) {
-  if (!c.opt.graphs || c.lv.size() < 2 || c.in_cycle_graph) return false;
-  if (!c.prof.on) return true;
-  const int k = c.prof.only;
-  if (k < 0) return false;
-  const auto& G = c.cgraph[which][0].state == 2 ? c.cgraph[which][0] : c.cgraph[which][1];
-  if (G.state == 2) return G.counts.launches[k] == 0;
-  return !(k == STOKES_KERNEL_TRANSFER || k == STOKES_KERNEL_BLAS1 || k == STOKES_KERNEL_OTHER ||
-           k == (which == 1 ? STOKES_KERNEL_SPMV_P1 : STOKES_KERNEL_SPMM_A3_COARSE));
+  if (!c.opt.graphs || c.graphs_off || c.lv.size() < 2 || c.in_cycle_graph) return false;
+  (void)which;
+  return !c.prof.on || c.prof.only >= 0;
 }
 
 // swaps the context's vector pool with a graph's private one for a scope
@@ -140,6 +139,141 @@ struct PoolSwap {
   PoolSwap(VecPool& x, VecPool& y) : a(x), b(y) { std::swap(a.free_, b.free_); }
   ~PoolSwap() { std::swap(a.free_, b.free_); }
 };
+
+// ---------------------------------------------------------------------------
+// The V-cycle below level 0 as an MgProgram (one cooperative kernel): the same
+// steps, coefficients and buffer ping-pong as vcycle() and cheb_run() on the
+// levels >= 1, recorded once with fixed buffers.
+// ---------------------------------------------------------------------------
+template <class T> static void mg_emit_cheb(stokes_ctx& c, MgProgram& P, const Csr& M, int nr, const T* dinv,
+                                           double lmin, double lmax, int steps, const T* b, T* x, bool xzero) {
+  const size_t len = (size_t)M.rows * nr;
+  T* d = c.arena.alloc<T>(len);
+  T* xt = c.arena.alloc<T>(len);
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta, rho = 1.0 / sigma;
+  T* xa = x;
+  T* xb = xt;
+  if (xzero && (steps - 1) % 2 == 1) std::swap(xa, xb);
+  auto csr_step = [&](const T* xin, T* xout, double c1, double c2) {
+    MgOp o;
+    o.kind = 4;
+    o.nr = nr;
+    o.rows = M.rows;
+    o.m = M.cols;
+    o.rp = M.rowptr;
+    o.col = M.col;
+    o.val = M.template v<T>();
+    o.b = b;
+    o.xin = xin;
+    o.d = d;
+    o.y = xout;
+    o.dinv = dinv;
+    o.c1 = c1;
+    o.c2 = c2;
+    P.add(o);
+    P.bytes += M.bytes(sizeof(T)) + (double)sizeof(T) * len * 6 + (double)sizeof(T) * M.rows;
+  };
+  if (xzero) {
+    MgOp o;
+    o.kind = 0;
+    o.nr = nr;
+    o.rows = M.rows;
+    o.b = b;
+    o.d = d;
+    o.y = xa;
+    o.dinv = dinv;
+    o.c1 = 1.0 / theta;
+    P.add(o);
+    P.bytes += (double)sizeof(T) * (3.0 * len + M.rows);
+  } else {
+    csr_step(xa, xb, 0.0, 1.0 / theta);
+    std::swap(xa, xb);
+  }
+  for (int k = 1; k < steps; ++k) {
+    double rn = 1.0 / (2.0 * sigma - rho);
+    csr_step(xa, xb, rn * rho, 2.0 * rn / delta);
+    std::swap(xa, xb);
+    rho = rn;
+  }
+  SK_REQUIRE(xa == x, STOKES_ERR_ARG, "multigrid program: odd post-smoothing step count");
+}
+
+template <class T> static void mg_emit_csr(stokes_ctx& c, MgProgram& P, int kind, const Csr& M, int nr,
+                                          const T* b, const T* x, T* y) {
+  MgOp o;
+  o.kind = kind;
+  o.nr = nr;
+  o.rows = M.rows;
+  o.m = M.cols;
+  o.rp = M.rowptr;
+  o.col = M.col;
+  o.val = M.template v<T>();
+  o.b = b;
+  o.xin = x;
+  o.y = y;
+  P.add(o);
+  P.bytes += M.bytes(sizeof(T)) + (double)sizeof(T) * nr * ((double)M.cols + M.rows * (kind == 1 ? 1.0 : 2.0));
+  (void)c;
+}
+
+template <class T> static void mg_emit_vcycle(stokes_ctx& c, MgProgram& P, int which, int l, const T* b, T* x) {
+  Level& L = c.lv[l];
+  const int nr = which == 1 ? 1 : 3;
+  const Csr& M = which == 1 ? L.KQ : L.A3;
+  if (l + 1 == (int)c.lv.size()) {
+    MgOp o;
+    o.kind = 5;
+    o.nr = nr;
+    o.m = M.rows;
+    o.val = which ? pick<T>(L.KQ_cinv64, L.KQ_cinv32) : pick<T>(L.A3_cinv64, L.A3_cinv32);
+    o.b = b;
+    o.y = x;
+    P.add(o);
+    P.bytes += (double)sizeof(T) * ((double)M.rows * M.rows + 2.0 * M.rows * nr);
+    return;
+  }
+  const T* dinv = which == 1 ? pick<T>(L.KQ_dinv64, L.KQ_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32);
+  const double lhat = which == 1 ? L.KQ_lmax : L.A3_lmax;
+  const int deg = std::max(1, c.opt.cheb_degree);
+  mg_emit_cheb<T>(c, P, M, nr, dinv, c.opt.cheb_low * lhat, c.opt.cheb_high * lhat, deg, b, x, true);
+  const size_t len = (size_t)M.rows * nr;
+  Level& Lc = c.lv[l + 1];
+  const size_t lenc = (size_t)(which == 1 ? Lc.KQ.rows : Lc.A3.rows) * nr;
+  T* r = c.arena.alloc<T>(len);
+  T* bc = c.arena.alloc<T>(lenc);
+  T* xc = c.arena.alloc<T>(lenc);
+  mg_emit_csr<T>(c, P, 3, M, nr, b, x, r);                                  // r = b - M x
+  mg_emit_csr<T>(c, P, 1, which == 1 ? L.R1 : L.R2, nr, nullptr, r, bc);   // bc = R r
+  mg_emit_vcycle<T>(c, P, which, l + 1, bc, xc);
+  mg_emit_csr<T>(c, P, 2, which == 1 ? L.P1 : L.P2, nr, nullptr, xc, x);   // x += P xc
+  mg_emit_cheb<T>(c, P, M, nr, dinv, c.opt.cheb_low * lhat, c.opt.cheb_high * lhat, deg, b, x, false);
+}
+
+// The program for the levels >= 1 of V-cycle kind `which` (0: A~_3, 1: eps
+// M_Q + L_Q), built on first use; its input b and output x are fixed buffers.
+template <class T> static MgProgram* mg_program(stokes_ctx& c, int which) {
+  auto& slot = c.mgprog[which][std::is_same<T, float>::value ? 1 : 0];
+  if (!slot) {
+    SK_REQUIRE(c.lv.size() >= 2, STOKES_ERR_ARG, "multigrid program needs two levels");
+    auto P = std::make_unique<MgProgram>();
+    const int nr = which == 1 ? 1 : 3;
+    const size_t len1 = (size_t)(which == 1 ? c.lv[1].KQ.rows : c.lv[1].A3.rows) * nr;
+    P->b = c.arena.alloc<T>(len1);
+    P->x = c.arena.alloc<T>(len1);
+    mg_emit_vcycle<T>(c, *P, which, 1, (const T*)P->b, (T*)P->x);
+    P->finalize(c.arena, std::is_same<T, float>::value);
+    slot = std::move(P);
+  }
+  return slot.get();
+}
+
+// the cooperative kernel serves V-cycles of A~_3 and eps M_Q + L_Q when the
+// hierarchy has a level below the first coarse one and the cycle uses
+// Chebyshev smoothing with an even number of steps after the first (so the
+// smoothed iterate ends in its own buffer)
+static bool coarse_kernel_ok(const stokes_ctx& c, int which) {
+  return c.opt.coarse_kernel && which != 2 && c.lv.size() >= 3 && std::max(1, c.opt.cheb_degree) % 2 == 0;
+}
 
 // x_1 = V-cycle below level 0 applied to b_1 (G.b -> G.x)
 template <class T> static void coarse_run(stokes_ctx& c, int which, stokes_ctx::CoarseGraph& G) {
@@ -209,14 +343,23 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
   const T* dinv = which == 1 ? pick<T>(L.KQ_dinv64, L.KQ_dinv32)
                              : (which == 2 ? pick<T>(L.AV_dinv64, L.AV_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32));
   const double lhat = which == 1 ? L.KQ_lmax : (which == 2 ? L.AV_lmax : L.A3_lmax);
-  double lmax = kChebHigh * lhat, lmin = kChebLow * lhat;
+  double lmax = c.opt.cheb_high * lhat, lmin = c.opt.cheb_low * lhat;
   int deg = std::max(1, c.opt.cheb_degree);
   const int kind = which == 1 ? STOKES_KERNEL_SPMV_P1 : (l == 0 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMM_A3_COARSE);
   cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind);
   Level& Lc = c.lv[l + 1];
   const Csr& Mc = level_op(Lc, which);
   size_t lenc = (size_t)Mc.rows * nr;
-  if (l == 0 && coarse_graph_ok(c, which)) {
+  if (l == 0 && coarse_kernel_ok(c, which)) {
+    MgProgram* P = mg_program<T>(c, which);
+    {
+      Tmp<T> r(c.pool, len);
+      level_resid<T>(c, M, nr, b, x, r, kind);
+      spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, (T*)P->b, STOKES_KERNEL_TRANSFER);
+    }
+    P->launch(c.ex);
+    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, (const T*)P->x, x, STOKES_KERNEL_TRANSFER);
+  } else if (l == 0 && coarse_graph_ok(c, which)) {
     auto& G = c.cgraph[which][std::is_same<T, float>::value ? 1 : 0];
     if (!G.b) {
       G.b = c.arena.raw(lenc * sizeof(T));
@@ -251,14 +394,9 @@ template <class T> static void vcycles_plain(stokes_ctx& c, int which, const T* 
 // a V-cycle of this kind.
 constexpr size_t kMaxCycleGraphs = 64;
 static bool cycle_graph_ok(const stokes_ctx& c, int which) {
-  if (!c.opt.graphs || c.in_cycle_graph) return false;
-  if (!c.prof.on) return true;
-  const int k = c.prof.only;
-  if (k < 0) return false;
-  const bool in_cycle = k == STOKES_KERNEL_TRANSFER || k == STOKES_KERNEL_BLAS1 || k == STOKES_KERNEL_OTHER ||
-                        k == STOKES_KERNEL_SPMM_A3_COARSE ||
-                        k == (which == 1 ? STOKES_KERNEL_SPMV_P1 : STOKES_KERNEL_SPMM_A3);
-  return !in_cycle;
+  if (!c.opt.graphs || c.graphs_off || c.in_cycle_graph) return false;
+  (void)which;
+  return !c.prof.on || c.prof.only >= 0;
 }
 
 // Sync-free regions (a whole V-cycle; C with fixed inner iterations) from
@@ -298,6 +436,20 @@ template <class Body> static void graph_region(stokes_ctx& c, const GraphKey& ke
     c.ex.s = c.cap_stream;
     try {
       body();
+    } catch (const Error& err) {
+      c.ex.s = launch;
+      c.prof.capture = nullptr;
+      cudaStreamEndCapture(c.cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      if (err.status != STOKES_ERR_CUDA) throw;
+      // a step this runtime cannot record (the cooperative coarse-level
+      // kernel): no more graphs for this context, run the region plainly
+      (void)cudaGetLastError();
+      c.graphs_off = true;
+      c.vgraphs.erase(it);
+      flag.f = false;
+      body();
+      return;
     } catch (...) {
       c.ex.s = launch;
       c.prof.capture = nullptr;
@@ -334,6 +486,7 @@ template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* 
 // the preconditioner of step k+1 runs, so the GPU never idles on the check.
 // ---------------------------------------------------------------------------
 // fixed > 0: exactly `fixed` iterations and no host synchronisation at all.
+// op(d, q, dq) computes q = M d and the device scalar *dq = d . q.
 template <class T, class Op, class Pre>
 static int pcg(stokes_ctx& c, size_t n, Op&& op, Pre&& pre, const T* b, T* x, double rtol, int maxit,
                bool* converged = nullptr, int fixed = 0) {
@@ -363,18 +516,17 @@ static int pcg(stokes_ctx& c, size_t n, Op&& op, Pre&& pre, const T* b, T* x, do
   bool done = false;
   const int cap = fixed > 0 ? fixed : maxit;
   while (it < cap) {
-    op((const T*)d, (T*)q);
-    dot1<T>(c, (const T*)d, (const T*)q, n, D + 2, kDotFast);
-    cg_update<T>(c.ex, n, Coef::ratio(D + irz, D + 2), d, x, q, r);
+    op((const T*)d, (T*)q, D + 2);
     ++it;
     if (fixed > 0) {
+      cg_update<T>(c.ex, n, Coef::ratio(D + irz, D + 2), d, x, q, r);
       if (it == cap) {
         done = true;
         break;
       }
       pre((const T*)r, (T*)z);
     } else {
-      dot1<T>(c, (const T*)r, (const T*)r, n, D + 3, kDotFast);
+      cg_update_rr<T>(c.ex, c.ds, n, Coef::ratio(D + irz, D + 2), d, x, q, r, D + 3);  // and r . r
       read_issue(c, D + 3, s + 3);
       pre((const T*)r, (T*)z);
       double rr = read_wait(c, s + 3);
@@ -385,7 +537,7 @@ static int pcg(stokes_ctx& c, size_t n, Op&& op, Pre&& pre, const T* b, T* x, do
       }
     }
     dot1<T>(c, (const T*)r, (const T*)z, n, D + irzn, kDotFast);
-    axpby<T>(c.ex, n, Coef::constant(1.0), z, Coef::ratio(D + irzn, D + irz), d);
+    axpby<T>(c.ex, n, Coef::constant(1.0), z, Coef::cg_ratio(D + irzn, D + irz), d);
     std::swap(irz, irzn);
   }
   if (converged) *converged = done;
@@ -413,7 +565,15 @@ template <class T> static void op_A(stokes_ctx& c, const T* x, T* y) {
 template <class T> static int ainv(stokes_ctx& c, const T* t, T* w, double tol) {
   bool ok = true;
   int it = pcg<T>(
-      c, nvel(c), [&](const T* x, T* y) { op_A<T>(c, x, y); },
+      c, nvel(c),
+      [&](const T* x, T* y, double* dq) {
+        if (c.gamma > 0.0) {
+          op_A<T>(c, x, y);
+          dot1<T>(c, x, (const T*)y, nvel(c), dq, kDotFast);
+        } else {
+          bsr3_apply_dot<T>(c.ex, c.A, x, y, c.ds, dq);  // d . A d fused into the product
+        }
+      },
       [&](const T* r, T* z) { vcycles<T>(c, velocity_cycle(c), r, z, std::max(1, c.opt.vcycles)); }, t, w, tol,
       c.opt.max_inner, &ok);
   c.inner_iters += it;
@@ -439,7 +599,7 @@ template <class T> static int cprec_body(stokes_ctx& c, const T* r, T* z) {
   const T* linv = pick<T>(c.lumped_inv64, c.lumped_inv32);
   int it = pcg<T>(
       c, np,
-      [&](const T* p, T* y) {
+      [&](const T* p, T* y, double* dq) {
         if (lumped) {
           Tmp<T> t(c.pool, nv);
           bt_apply<T>(c.ex, c.Bt, p, t, linv, (const T*)nullptr, 1.0);
@@ -456,6 +616,7 @@ template <class T> static int cprec_body(stokes_ctx& c, const T* r, T* z) {
           spmv_store<T>(c.ex, c.LQ, 1, p, y, STOKES_KERNEL_SPMV_P1);
         }
         project_mean<T>(c, y, np, kDotFast);
+        dot1<T>(c, p, (const T*)y, np, dq, kDotFast);
       },
       [&](const T* v, T* w) {
         Tmp<T> vp(c.pool, np);
@@ -472,12 +633,8 @@ template <class T> static int cprec_body(stokes_ctx& c, const T* r, T* z) {
 // is replayed from a graph (keyed by r, z and the device-scalar stack depth,
 // whose slots it uses) when none of its launches is being timed per class.
 static bool cprec_graph_ok(const stokes_ctx& c) {
-  if (!c.opt.graphs || c.in_cycle_graph || c.opt.schur_inner_iters <= 0) return false;
-  if (!c.prof.on) return true;
-  const int k = c.prof.only;
-  if (k < 0) return false;
-  return k == STOKES_KERNEL_SPMV_A || k == STOKES_KERNEL_RESIDUAL || k == STOKES_KERNEL_SPMM_A3_COARSE ||
-         (k == STOKES_KERNEL_SPMM_A3 && c.opt.schur_prec != STOKES_SCHUR_PREC_MASS);
+  if (!c.opt.graphs || c.graphs_off || c.in_cycle_graph || c.opt.schur_inner_iters <= 0) return false;
+  return !c.prof.on || c.prof.only >= 0;
 }
 
 template <class T> static void cprec(stokes_ctx& c, const T* r, T* z) {
@@ -559,7 +716,7 @@ static void method1(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
     dots<T>(c.ex, c.ds, 1, xs, ys, np, D + irzn, kDotExact);
     dots<T>(c.ex, c.ds, 1, xs + 1, ys + 1, np, D + 3, kDotExact);
     scalar_sub(c.ex, D + 5, D + irzn, D + 3);
-    axpby<T>(c.ex, np, Coef::constant(1.0), z, Coef::ratio(D + 5, D + irz), d);
+    axpby<T>(c.ex, np, Coef::constant(1.0), z, Coef::cg_ratio(D + 5, D + irz), d);
     std::swap(irz, irzn);
   }
   c.outer_iters += k;
@@ -757,6 +914,13 @@ static void correction(stokes_ctx& c, const double* rF, const double* rg, double
   add_convert<T, double>(c.ex, np, dP, P);
 }
 
+static int read_flag(stokes_ctx& c) {
+  int flag = 0;
+  SK_CUDA(cudaMemcpyAsync(&flag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  return flag;
+}
+
 // full residual rF = F - A U + B^T P, rg = g - B U and its relative norm
 static double full_residual(stokes_ctx& c, const double* F, const double* g, const double* U, const double* P,
                             double* rF, double* rg, double normFg) {
@@ -820,6 +984,7 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
   double rel = 0.0;
   int pass = 0;
   if (normFg > 0) {
+   try {
     for (;; ++pass) {
       rel = full_residual(c, F, gp, U, P, rF, rg, normFg);
       if (!std::isfinite(rel)) {
@@ -831,18 +996,25 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
         status = STOKES_ERR_NOT_CONVERGED;
         break;
       }
-      if (c.mixed) {
-        // FP32 inner work: each pass asks for a reduction of pass_tol and its inner
-        // velocity solves for pass_tol / 30 (measured best on the 48^3 workload:
-        // cheap passes, about three of them to reach 1e-8)
-        double eta = std::max(c.opt.pass_tol, 0.5 * tol / rel);
-        double tin = std::max(c.opt.inner_tol, c.opt.pass_tol / 30.0);
+      // Pass schedule: each pass asks for a reduction of pass_tol and its inner
+      // velocity solves for pass_tol / 30 (measured best on the 48^3 workload:
+      // cheap passes, about three of them to reach 1e-8); the default for FP32
+      // inner work. Otherwise one pass aims straight at tol with inner solves
+      // at inner_tol (the paper's setting; the FP64 default).
+      const bool passes = c.opt.pass_schedule == 1 || (c.opt.pass_schedule == 0 && c.mixed);
+      double eta = passes ? std::max(c.opt.pass_tol, 0.5 * tol / rel) : std::max(0.5 * tol / rel, 1e-13);
+      double tin = passes ? std::max(c.opt.inner_tol, c.opt.pass_tol / 30.0) : c.opt.inner_tol;
+      if (c.mixed)
         correction<float>(c, rF, rg, U, P, eta, tin);
-      } else {
-        double eta = std::max(0.5 * tol / rel, 1e-13);
-        correction<double>(c, rF, rg, U, P, eta, c.opt.inner_tol);
-      }
+      else
+        correction<double>(c, rF, rg, U, P, eta, tin);
     }
+   } catch (const Error& e) {
+    // a non-finite residual after a flagged breakdown is the breakdown
+    if (e.status == STOKES_ERR_NAN && (read_flag(c) & 1))
+      throw Error(STOKES_ERR_BREAKDOWN, std::string("Krylov breakdown (r^T z <= 0 or p^T A p <= 0), then ") + e.what());
+    throw;
+   }
   }
   // int p_h = 0: P -= (M_Q 1 . P) / (1^T M_Q 1)
   {
@@ -851,10 +1023,10 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
     sub_mean<double>(c.ex, np, c.sc.d + s2, c.MQ1_sum, P);
     c.sc.give(1);
   }
-  int flag = 0;
-  SK_CUDA(cudaMemcpyAsync(&flag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.ex.s));
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
-  if (status == STOKES_OK && (flag & 1) && rel > tol) status = STOKES_ERR_BREAKDOWN;
+  const int flag = read_flag(c);
+  // a failed solve that met r^T z <= 0 or p^T A p <= 0 on the way broke down
+  if ((status == STOKES_ERR_NOT_CONVERGED || status == STOKES_ERR_NAN) && (flag & 1)) status = STOKES_ERR_BREAKDOWN;
+  if (flag & 4) status = STOKES_ERR_TIMEOUT;  // a bounded device wait expired
   if (info) {
     info->outer_iters = c.outer_iters;
     info->inner_iters = c.inner_iters;

@@ -7,6 +7,7 @@
 // timing sweep at setup.
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -42,6 +43,8 @@ void Prof::reset() {
     r.ev.clear();
     r.bytes = 0;
     r.launches = 0;
+    r.ev_bytes = 0;
+    r.ev_launches = 0;
   }
 }
 
@@ -62,6 +65,8 @@ ProfScope::ProfScope(const Exec& e, int k, double bytes) : ex(e), kind(k) {
     if (ex.prof->only < 0 || ex.prof->only == kind) {
       e1 = ex.prof->get();
       cudaEventRecord(e1, ex.s);
+      ex.prof->rec[kind].ev_bytes += bytes;
+      ex.prof->rec[kind].ev_launches += 1;
     }
   }
 }
@@ -261,34 +266,6 @@ __global__ void __launch_bounds__(256) k_bsr3(int rows, const int* __restrict__ 
   if (row < rows && lane == 0) epi(row, acc);
 }
 
-// ---------------------------------------------------------------------------
-// double-float BSR3 residual. Error-free transformations (published methods):
-// TwoProduct with an FMA, p + e = a * b exactly (Ogita, Rump & Oishi 2005);
-// TwoSum, s + e = a + b exactly (Knuth, TAOCP vol. 2, 4.2.2). The _rn
-// intrinsics keep the compiler from contracting these steps into FMAs.
-// ---------------------------------------------------------------------------
-struct DF {
-  float h, l;
-};
-// s += (ah + al) * (xh + xl), dropping al * xl (2^-48 relative)
-__device__ __forceinline__ void df_madd(DF& s, float ah, float al, float xh, float xl) {
-  const float ph = __fmul_rn(ah, xh);
-  const float pe = __fmaf_rn(ah, xh, -ph);
-  const float pc = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
-  const float t = __fadd_rn(s.h, ph);
-  const float z = __fsub_rn(t, s.h);
-  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(ph, z));
-  s.h = t;
-  s.l = __fadd_rn(s.l, __fadd_rn(e, __fadd_rn(pe, pc)));
-}
-__device__ __forceinline__ void df_add(DF& s, float oh, float ol) {
-  const float t = __fadd_rn(s.h, oh);
-  const float z = __fsub_rn(t, s.h);
-  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(oh, z));
-  s.h = t;
-  s.l = __fadd_rn(s.l, __fadd_rn(ol, e));
-}
-
 template <int G>
 __global__ void __launch_bounds__(256) k_bsr3_df(int rows, const int* __restrict__ rp, const int* __restrict__ col,
                                                  const float* __restrict__ vh, const float* __restrict__ vl,
@@ -359,6 +336,12 @@ static void launch_bsr3_df(const Exec& ex, const Csr& m, const float* xh, const 
 
 void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y,
                       int kind) {
+  if (m.sym && m.sym->v32 && m.sym->v32lo) {
+    // hi and lo values once, x hi and lo gathered once, b read, y written
+    ProfScope ps(ex, kind, (double)m.sym->total * 8.0 + 8.0 * 3 * m.rows + 16.0 * 3 * m.rows);
+    sym3_residual_df(ex, m, xh, xl, b, y);
+    return;
+  }
   SK_REQUIRE(m.v32 && m.v32lo && m.br == 3 && m.bc == 3, STOKES_ERR_ARG, "double-float residual needs A hi/lo");
   // matrix hi+lo planes, column indices, x hi+lo gathered once, b read, y written
   ProfScope ps(ex, kind, (double)m.nnz * (4.0 + 8.0 * 9) + 4.0 * (m.rows + 1) + 8.0 * 3 * m.cols +
@@ -371,6 +354,93 @@ void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float
     case 16: launch_bsr3_df<16>(ex, m, xh, xl, b, y); break;
     default: launch_bsr3_df<32>(ex, m, xh, xl, b, y); break;
   }
+}
+
+// y = A x with 3x3 blocks and *dot = x . y (own-row components of x), the dot
+// reduced over the grid in a fixed order (grid_sum); every thread reaches it
+template <int G, class T>
+__global__ void __launch_bounds__(256) k_bsr3_dot(int rows, const int* __restrict__ rp, const int* __restrict__ col,
+                                                  const T* __restrict__ v, long long nnz, const T* __restrict__ x,
+                                                  size_t xs, T* __restrict__ y, double* partial, unsigned* counter,
+                                                  double* dot) {
+  constexpr int U = Batch<G>::U > 4 ? 4 : Batch<G>::U;
+  // a grid of one resident wave walks the row groups (grid stride), so the
+  // grid sum below takes one counter increment per resident block, not per
+  // row group
+  const int lane = threadIdx.x & (G - 1);
+  const int groups = (int)(((long long)rows * G + blockDim.x - 1) / blockDim.x);
+  double part = 0.0;
+  for (int gb = blockIdx.x; gb < groups; gb += gridDim.x) {
+    const int row = (gb * (int)blockDim.x + (int)threadIdx.x) / G;
+    T acc[3] = {T(0), T(0), T(0)};
+    if (row < rows) {
+      const int e = rp[row + 1];
+      for (int k = rp[row] + lane; k < e; k += U * G) {
+        int c[U];
+        T a[U][9];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int kk = k + u * G;
+          const bool ok = kk < e;
+          const int ks = ok ? kk : e - 1;  // in-bounds re-read, zero contribution
+          c[u] = col[ks];
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            const T av = v[(size_t)j * nnz + ks];
+            a[u][j] = ok ? av : T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const T x0 = x[c[u]], x1 = x[xs + c[u]], x2 = x[2 * xs + c[u]];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) acc[r] += a[u][3 * r] * x0 + a[u][3 * r + 1] * x1 + a[u][3 * r + 2] * x2;
+        }
+      }
+    }
+    group_reduce<G, T, 3>(acc);
+    if (row < rows && lane == 0) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const size_t i = r * xs + row;
+        y[i] = acc[r];
+        part += (double)(acc[r] * x[i]);
+      }
+    }
+  }
+  grid_sum(part, partial, counter, dot);
+}
+
+// one resident wave of a kernel: SMs x resident blocks per SM (at most `want`)
+template <class K> static int resident_grid(K kernel, int block, int want) {
+  int dev = 0, sms = 0, occ = 0;
+  SK_CUDA(cudaGetDevice(&dev));
+  SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0));
+  return std::max(1, std::min(want, sms * std::max(1, occ)));
+}
+
+template <int G, class T>
+static void launch_bsr3_dot(const Exec& ex, const Csr& m, const T* x, T* y, const DotScratch& ds, double* dot) {
+  const int want = cdiv((long long)m.rows * G, 256);
+  if (want == 0) return;
+  static thread_local int cached[2][6] = {};  // resident wave per (precision, group width)
+  int& slot = cached[sizeof(T) == 4][__builtin_ctz(G)];
+  if (!slot) slot = resident_grid(k_bsr3_dot<G, T>, 256, 1 << 30);
+  const int grid = std::min(want, slot);
+  SK_REQUIRE(ds.fused_partial && grid <= ds.fused_cap, STOKES_ERR_ARG, "fused dot scratch too small");
+  k_bsr3_dot<G, T><<<grid, 256, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, (size_t)m.cols, y,
+                                           ds.fused_partial, ds.fused_counter, dot);
+  SK_CHECK_LAUNCH();
+}
+
+// upper bound on the blocks of a dot-fused BSR3 launch (one resident wave of
+// 256-thread blocks: at most 8 per SM)
+int bsr3_dot_grid(const Csr& m) {
+  int dev = 0, sms = 0;
+  SK_CUDA(cudaGetDevice(&dev));
+  SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return std::min(cdiv((long long)m.rows * 32, 256), 8 * sms);
 }
 
 // 1x3 blocks: B (P1 rows, interior P2 node columns)
@@ -447,6 +517,17 @@ __global__ void __launch_bounds__(256) k_bt(int rows, const int* __restrict__ rp
   if (row < rows && lane == 0) epi(row, acc);
 }
 
+static_assert(kStencilVec == 4, "the stencil kernel loads four entries' weights per vector");
+template <class T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+__device__ __forceinline__ float4 ldcs_vec(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ double4 ldcs_vec(const double4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldcs(q), b = __ldcs(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
 // Stencil-structured product (StencilOp): one thread per row; a block holds
 // rows of one class, so the entry loop, offsets and strides are uniform
 // across the warp and consecutive lanes gather from nodes 2 apart.
@@ -469,20 +550,27 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
   T acc[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc[q] = T(0);
-  const TM* vr = v + a.voff[c] + r;
+  // kStencilVec consecutive entries' weights per vector load
+  using V4 = typename Vec4<TM>::type;
+  const V4* vr = reinterpret_cast<const V4*>(v + a.voff[c]) + r;
   const size_t rc = (size_t)a.prows[c];
-  const int S = a.S[c], db = a.dbeg[c];
+  const int S4 = a.S[c] / kStencilVec, db = a.dbeg[c];
   // Entries whose neighbour lies outside the index space are stored as 0; their
   // linear index may fall on another node or, near the first and last planes,
   // outside the vector, so it is clamped into [0, xs): every row takes the same
   // branch-free loop and the zero weight cancels the clamped read.
   const int last = (int)xs - 1;
-#pragma unroll 4
-  for (int e = 0; e < S; ++e) {
-    const T w = (T)__ldcs(&vr[e * rc]);  // streamed once: evict first
-    const size_t cc = (size_t)min(max(row + a.lin[db + e], 0), last);
+#pragma unroll 2
+  for (int e4 = 0; e4 < S4; ++e4) {
+    const V4 w4 = ldcs_vec(&vr[e4 * rc]);  // streamed once: evict first
+    const TM wv[4] = {w4.x, w4.y, w4.z, w4.w};
+    size_t cc[4];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) acc[q] += w * x[q * xs + cc];
+    for (int j = 0; j < 4; ++j) cc[j] = (size_t)min(max(row + a.lin[db + 4 * e4 + j], 0), last);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * x[q * xs + cc[j]];
   }
   epi(row, acc);
 }
@@ -506,10 +594,12 @@ template <class T> static inline bool use_stencil(const Csr& m) {
   return m.st != nullptr && m.st->template v<T>() != nullptr;
 }
 
+// algorithmic bytes: the matrix's stored entries (not the zero padding), x
+// gathered once, the output and the epilogue's other vectors once
 static double stencil_bytes(const StencilOp& so, int esz, int nr, int streams) {
   long long rows = 0;
   for (int c = 0; c < so.ncls; ++c) rows += so.rows[c];
-  return (double)so.total * esz + (double)esz * rows * nr * (1 + streams);
+  return (double)so.total_real * esz + (double)esz * rows * nr * (1 + streams);
 }
 
 // ---------------------------------------------------------------------------
@@ -619,10 +709,42 @@ template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, cons
   launch(ex, m, SH_BSR3, xin, EpiCheb3<T>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
 }
 template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, int kind) {
+  if (m.sym && m.sym->template v<T>() && m.sym_products) {
+    ProfScope ps(ex, kind, sym3_bytes(*m.sym, sizeof(T), m.rows, b ? 1 : 0));
+    sym3_launch<T>(ex, m, x, y, b, nullptr, nullptr);
+    return;
+  }
   ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), 3, 3, b ? 1 : 0));
   if (b) launch(ex, m, SH_BSR3, x, EpiResid<T, 3>{b, y, (size_t)m.rows}, m.group);
   else launch(ex, m, SH_BSR3, x, EpiStore<T, 3>{y, (size_t)m.rows}, m.group);
 }
+template <class T> bool bsr3_apply_dot(const Exec& ex, const Csr& m, const T* x, T* y, const DotScratch& ds,
+                                       double* dot) {
+  if (m.sym && m.sym->template v<T>() && m.sym_products && ds.fused_partial && sym3_grid(*m.sym) <= ds.fused_cap) {
+    // the product's bytes plus the own-row x read of the fused dot
+    ProfScope ps(ex, STOKES_KERNEL_SPMV_A, sym3_bytes(*m.sym, sizeof(T), m.rows, 1));
+    sym3_launch<T>(ex, m, x, y, (const T*)nullptr, &ds, dot);
+    return true;
+  }
+  if (m.template v<T>() && ds.fused_partial && bsr3_dot_grid(m) <= ds.fused_cap) {
+    ProfScope ps(ex, STOKES_KERNEL_SPMV_A, prod_bytes(m, sizeof(T), 3, 3, 1));
+    switch (m.group) {
+      case 1: launch_bsr3_dot<1, T>(ex, m, x, y, ds, dot); break;
+      case 2: launch_bsr3_dot<2, T>(ex, m, x, y, ds, dot); break;
+      case 4: launch_bsr3_dot<4, T>(ex, m, x, y, ds, dot); break;
+      case 8: launch_bsr3_dot<8, T>(ex, m, x, y, ds, dot); break;
+      case 16: launch_bsr3_dot<16, T>(ex, m, x, y, ds, dot); break;
+      default: launch_bsr3_dot<32, T>(ex, m, x, y, ds, dot); break;
+    }
+    return true;
+  }
+  bsr3_apply<T>(ex, m, x, y, (const T*)nullptr);
+  const T* xs[1] = {x};
+  const T* ys[1] = {y};
+  dots<T>(ex, ds, 1, xs, ys, (size_t)m.rows * 3, dot, kDotFast);
+  return false;
+}
+
 template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha) {
   ProfScope ps(ex, STOKES_KERNEL_B, m.bytes(sizeof(T)) + sizeof(T) * (3.0 * m.cols + m.rows * (b ? 2.0 : 1.0)));
   launch(ex, m, SH_B, x, EpiAxpy<T, 1>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group);
@@ -793,7 +915,8 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   template void bsr3_cheb<T>(const Exec&, const Csr&, const T*, const T*, T*, T*, const T*, double, double, int); \
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double);                     \
   template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double);          \
-  template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*);
+  template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*);                          \
+  template bool bsr3_apply_dot<T>(const Exec&, const Csr&, const T*, T*, const DotScratch&, double*);
 SK_INST(float)
 SK_INST(double)
 

@@ -140,3 +140,43 @@ def test_largest_configuration_manufactured_errors_96(coupled96):
     rp = np.log2(errs[0][1] / errs[1][1])
     print(f"manufactured L2 errors 48^3 {errs[0]}, 96^3 {errs[1]}: rates velocity {ru:.2f}, pressure {rp:.2f}")
     assert ru > 2.65 and rp > 1.65, (errs, ru, rp)
+
+
+def test_indefinite_smoother_reports_breakdown():
+    """A Chebyshev smoothing interval far below the spectrum of D^{-1} A~_3
+    ([0.01, 0.05] x lambda_max instead of [0.1, 1.1]) over-relaxes the high
+    modes, so the V-cycle preconditioner is indefinite: the inner PCG meets
+    r^T z <= 0, the device flags it, and the failed solve is reported as a
+    Krylov breakdown rather than as a plain failure to converge."""
+    sk = gpu_module()
+    n = 8
+    V = wl.kuhn_vertices(n, 0.2, 4)
+    f = wl.random_force(n, 5)
+    S = sk.Stokes(n, V, 0.1, 1e-2, options=sk.stokes_default_options(cheb_low=0.01, cheb_high=0.05,
+                                                                      max_refine=2, max_inner=50, max_outer=20))
+    with pytest.raises(sk.StokesError) as err:
+        S.solve(cuda(f), None, 1e-10)
+    assert err.value.status == -5, str(err.value)       # STOKES_ERR_BREAKDOWN
+    S.close()
+    # the default interval on the same problem converges
+    S = sk.Stokes(n, V, 0.1, 1e-2)
+    _, _, info = S.solve(cuda(f), None, 1e-10)
+    assert info.status == 0
+    S.close()
+
+
+def test_bounded_device_wait_expires_and_context_stays_usable():
+    """The cooperative coarse-level kernel separates its steps with grid-wide
+    barriers whose waits are bounded. A barrier that nothing completes must
+    give up (about a second), report STOKES_ERR_TIMEOUT, and leave the context
+    usable: a solve with the cooperative kernel afterwards succeeds."""
+    sk = gpu_module()
+    n = 8
+    V = wl.kuhn_vertices(n, 0.2, 4)
+    S = sk.Stokes(n, V, 0.1, 1e-2, options=sk.stokes_default_options(coarse_kernel=1))
+    st = sk._L.stokes_check_bounded_wait(S.ctx)
+    assert st == -7, st                                   # STOKES_ERR_TIMEOUT
+    f = wl.random_force(n, 5)
+    _, _, info = S.solve(cuda(f), None, 1e-10)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    S.close()

@@ -31,3 +31,33 @@ def test_outer_iterations_flat_in_h(method, dt_rule):
     print("method", method, "dt", dt_rule, "outer iterations n=8,16,32:", iters)
     assert max(iters) <= 1.5 * min(iters) + 2, iters
     assert iters[-1] <= iters[-2] + 3, iters
+
+
+def test_pressure_laplacian_preconditioner_iterations_recorded():
+    """The paper finds the pressure-Laplacian Cahouet-Chabard preconditioner
+    C^Delta less robust than C^Lambda (Remark on L_Q, Sec. 6.1, Fig.
+    residuals_C2). Both are run here on the same problems over h (n = 8, 16,
+    32) and mu (1, 1e-2, 1e-4), FP64, dt = 1e-3, to 1e-8; the outer Schur-CG
+    iteration counts are printed side by side. Every solve must converge; the
+    C^Lambda counts must stay bounded in h (the robustness the paper reports
+    for it), while for C^Delta the counts are recorded, not bounded."""
+    sk = gpu_module()
+    table = {}
+    for mu in (1.0, 1e-2, 1e-4):
+        for prec in (0, 1):
+            row = []
+            for n in (8, 16, 32):
+                V = wl.kuhn_vertices(n, 0.2, 1)
+                f = wl.manufactured_force(n, V, mu, 1e-3, 1)
+                opt = sk.stokes_default_options(schur_prec=prec, pass_schedule=2)
+                S = sk.Stokes(n, V, mu, 1e-3, 0.0, opt)
+                _, _, info = S.solve(cuda(f), None, 1e-8)
+                assert info.status == 0 and info.rel_residual <= 1e-8, (mu, prec, n, info.as_dict())
+                row.append(info.outer_iters)
+                S.close()
+            table[(mu, "C^Lambda" if prec == 0 else "C^Delta")] = row
+    for (mu, name), row in table.items():
+        print(f"mu={mu:g} {name}: outer iterations n=8,16,32: {row}")
+    for mu in (1.0, 1e-2, 1e-4):
+        lam = table[(mu, "C^Lambda")]
+        assert max(lam) <= 1.5 * min(lam) + 2, (mu, lam)
