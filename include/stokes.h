@@ -153,6 +153,11 @@ typedef struct {
                             An interval far below the spectrum makes the
                             V-cycle indefinite; the Krylov solvers then report
                             STOKES_ERR_BREAKDOWN. */
+  int sym_batch;         /* symmetric A products: block entries whose loads one
+                            thread issues before using them (2, 4 or 8; 0:
+                            default 8) */
+  int stencil_min_rows;  /* formats 0 and 3: levels with at least this many rows
+                            use stencil storage (0: 2^18) */
 } stokes_options;
 
 typedef struct {

@@ -40,7 +40,8 @@ class StokesOptions(C.Structure):
         ("schur_inner_iters", C.c_int), ("pass_tol", C.c_double), ("format", C.c_int),
         ("graphs", C.c_int), ("vel_prec", C.c_int), ("mass_steps_v", C.c_int),
         ("coarse_kernel", C.c_int), ("pass_schedule", C.c_int),
-        ("cheb_low", C.c_double), ("cheb_high", C.c_double),
+        ("cheb_low", C.c_double), ("cheb_high", C.c_double), ("sym_batch", C.c_int),
+        ("stencil_min_rows", C.c_int),
     ]
 
     def as_dict(self):

@@ -14,6 +14,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <set>
 #include <vector>
 
@@ -576,6 +577,121 @@ __global__ void __launch_bounds__(128) k_load(LoadArgs a) {
   }
   const size_t nvi = (size_t)(2 * a.n - 1) * (2 * a.n - 1) * (2 * a.n - 1);
   for (int c = 0; c < 3; ++c) a.F[c * nvi + row] += tg.vol * s[c] / 420.0;  // component-major
+}
+
+// |K| of every tetrahedron, index 6 * cube + p (cube lexicographic, x fastest)
+__global__ void k_tet_volumes(int n, const double* __restrict__ X, double* __restrict__ vol) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 6LL * n * n * n) return;
+  const int p = (int)(t % 6);
+  const long long cube = t / 6;
+  const int i = (int)(cube % n), j = (int)((cube / n) % n), k = (int)(cube / ((long long)n * n));
+  TetGeom tg;
+  tet_geometry(n, X, i, j, k, p, tg);
+  vol[t] = tg.vol;
+}
+
+static void upload_tet_nodes();
+void tet_volumes(const Exec& ex, int n, const double* X, double* vol) {
+  {  // the node table of the load kernel, once per device (setup runs before any solve)
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && !done[dev]) {
+      upload_tet_nodes();
+      done[dev] = true;
+    }
+  }
+  const long long T = 6LL * n * n * n;
+  k_tet_volumes<<<cdiv(T, 256), 256, 0, ex.s>>>(n, X, vol);
+  SK_CHECK_LAUNCH();
+}
+
+// Half-grid offset (0..2 per axis, packed as ox + 3 oy + 9 oz) of local node a
+// of tetrahedron p within its cube (host table, uploaded once).
+__constant__ signed char c_tet_node[6][10];
+static void upload_tet_nodes() {
+  signed char tab[6][10];
+  for (int p = 0; p < 6; ++p) {
+    int v[4][3];
+    ref_tet(p, v);
+    for (int a = 0; a < 10; ++a) {
+      int q[3];
+      for (int c = 0; c < 3; ++c)
+        q[c] = a < 4 ? 2 * v[a][c] : v[kEdge[a - 4][0]][c] + v[kEdge[a - 4][1]][c];
+      tab[p][a] = (signed char)(q[0] + 3 * q[1] + 9 * q[2]);
+    }
+  }
+  SK_CUDA(cudaMemcpyToSymbol(c_tet_node, tab, sizeof(tab)));
+}
+
+// F = M_V f_h with the tet volumes precomputed: one launch per cube colour and
+// one thread per (cube, node of the cube's 3x3x3 half-grid block); the thread
+// adds the contributions of every tet of the cube that holds its node
+// (|K| sum_b M_ab f_b / 420 over the tet's nodes b), tets in order.
+__global__ void __launch_bounds__(128) k_load_vol(LoadArgs a, const double* __restrict__ vol) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.mx * a.my * a.mz * 27) return;
+  const int nu = t % 27;
+  t /= 27;
+  const int i = 2 * (t % a.mx) + a.cx;
+  const int j = 2 * ((t / a.mx) % a.my) + a.cy;
+  const int k = 2 * (t / (a.mx * a.my)) + a.cz;
+  const int q[3] = {2 * i + nu % 3, 2 * j + (nu / 3) % 3, 2 * k + nu / 9};
+  const int row = p2_interior_index(a.n, q);
+  if (row < 0) return;
+  const int N = 2 * a.n + 1;
+  const size_t base = (size_t)(2 * i) + N * ((size_t)(2 * j) + (size_t)N * (2 * k));
+  const size_t cube = (size_t)i + (size_t)a.n * ((size_t)j + (size_t)a.n * k);
+  double s[3] = {0, 0, 0};
+  for (int p = 0; p < 6; ++p) {
+    int la = -1;
+    for (int l = 0; l < 10; ++l)
+      if (c_tet_node[p][l] == nu) la = l;
+    if (la < 0) continue;
+    double tp[3] = {0, 0, 0};
+    for (int b = 0; b < 10; ++b) {
+      const int o = c_tet_node[p][b];
+      const size_t gid = base + (size_t)(o % 3) + N * ((size_t)((o / 3) % 3) + (size_t)N * (o / 9));
+      const double m = p2_mass420(la, b);
+      for (int c = 0; c < 3; ++c) tp[c] += m * a.f[3 * gid + c];
+    }
+    const double w = vol[6 * cube + p] / 420.0;
+    for (int c = 0; c < 3; ++c) s[c] += w * tp[c];
+  }
+  const size_t nvi = (size_t)(2 * a.n - 1) * (2 * a.n - 1) * (2 * a.n - 1);
+  for (int c = 0; c < 3; ++c) a.F[c * nvi + row] += s[c];  // component-major
+}
+
+void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat, const double* f_all, double* F,
+                   const double* vol) {
+  if (vol) {
+    SK_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * 3 * (size_t)p2pat.rows, ex.s));
+    ProfScope ps(ex, STOKES_KERNEL_OTHER, 24.0 * (double)(2 * n + 1) * (2 * n + 1) * (2 * n + 1) + 48.0 * p2pat.rows +
+                                              48.0 * n * n * n);
+    LoadArgs a{};
+    a.n = n;
+    a.X = X;
+    a.f = f_all;
+    a.F = F;
+    for (int colour = 0; colour < 8; ++colour) {
+      a.cx = colour & 1;
+      a.cy = (colour >> 1) & 1;
+      a.cz = (colour >> 2) & 1;
+      a.mx = (n - a.cx + 1) / 2;
+      a.my = (n - a.cy + 1) / 2;
+      a.mz = (n - a.cz + 1) / 2;
+      const int cubes = a.mx * a.my * a.mz;
+      if (cubes == 0) continue;
+      k_load_vol<<<cdiv((long long)cubes * 27, 128), 128, 0, ex.s>>>(a, vol);
+      if (colour > 0 && ex.prof && ex.prof->on) ex.prof->rec[STOKES_KERNEL_OTHER].launches += 1;
+      SK_CHECK_LAUNCH();
+    }
+    return;
+  }
+  assemble_load(ex, n, X, p2pat, f_all, F);
 }
 
 void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat, const double* f_all, double* F) {

@@ -169,6 +169,143 @@ void dots(const Exec& ex, const DotScratch& ds, int k, const T* const* x, const 
   SK_CHECK_LAUNCH();
 }
 
+// ---------------------------------------------------------------------------
+// Multi-vector kernels for the Arnoldi process (classical Gram-Schmidt):
+// out[i] = V_i . w for up to kMaxBasis vectors in one pass that reads w once,
+// and w -= sum_i h_i V_i in one pass. FP64 accumulation in a fixed order.
+// ---------------------------------------------------------------------------
+template <class T> struct MultiArgs {
+  const T* v[kMaxBasis];
+  double c[kMaxBasis];     // host coefficients (when dev == nullptr)
+  const double* dev;       // device coefficients h[0..k-1], or null
+  int k;
+  double sign;
+  size_t n;
+  T* w;
+  const T* wr;             // w for the dot kernel
+  double* partial;         // [k][gridDim.x]
+  unsigned* counter;
+  double* out;
+};
+
+// K: the compile-time bound (a power of two >= a.k), so the basis pointers and
+// accumulators are indexed statically
+template <class T, int K>
+__global__ void __launch_bounds__(256) k_mdot(MultiArgs<T> a) {
+  double s[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) s[i] = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.n; e += (size_t)gridDim.x * blockDim.x) {
+    const double we = (double)a.wr[e];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < a.k) s[i] += (double)a.v[i][e] * we;
+  }
+  __shared__ double sh[8][K];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    double v = s[i];
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < a.k) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+    a.partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the last block: for each vector, the partials in block order (one warp per vector)
+  for (int i = wid; i < a.k; i += (int)(blockDim.x >> 5)) {
+    double v = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(&a.partial[(size_t)i * gridDim.x + b]);
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.out[i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(256) k_maxpy(MultiArgs<T> a) {
+  __shared__ T h[K];
+  if (threadIdx.x < K) h[threadIdx.x] = threadIdx.x < a.k ? (T)(a.sign * (a.dev ? a.dev[threadIdx.x] : a.c[threadIdx.x])) : T(0);
+  __syncthreads();
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.n; e += (size_t)gridDim.x * blockDim.x) {
+    T acc = a.w[e];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < a.k) acc += h[i] * a.v[i][e];
+    a.w[e] = acc;
+  }
+}
+
+static inline int pow2_at_least(int k) {
+  int K = 1;
+  while (K < k) K <<= 1;
+  return K;
+}
+
+template <class T>
+void mdot(const Exec& ex, const DotScratch& ds, int k, const T* const* V, const T* w, size_t n, double* out) {
+  SK_REQUIRE(k >= 1 && k <= kMaxBasis, STOKES_ERR_ARG, "mdot: bad count");
+  const int grid = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, cdiv((long long)n, 256)));
+  SK_REQUIRE(ds.fused_partial && (long long)grid * k <= ds.fused_cap, STOKES_ERR_ARG, "mdot: scratch too small");
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * (k + 1.0));
+  MultiArgs<T> a{};
+  for (int i = 0; i < k; ++i) a.v[i] = V[i];
+  a.k = k;
+  a.n = n;
+  a.wr = w;
+  a.partial = ds.fused_partial;
+  a.counter = ds.fused_counter;
+  a.out = out;
+  switch (pow2_at_least(k)) {
+    case 1: k_mdot<T, 1><<<grid, 256, 0, ex.s>>>(a); break;
+    case 2: k_mdot<T, 2><<<grid, 256, 0, ex.s>>>(a); break;
+    case 4: k_mdot<T, 4><<<grid, 256, 0, ex.s>>>(a); break;
+    case 8: k_mdot<T, 8><<<grid, 256, 0, ex.s>>>(a); break;
+    case 16: k_mdot<T, 16><<<grid, 256, 0, ex.s>>>(a); break;
+    default: k_mdot<T, 32><<<grid, 256, 0, ex.s>>>(a); break;
+  }
+  SK_CHECK_LAUNCH();
+}
+
+template <class T>
+void maxpy(const Exec& ex, int k, const double* dev_coef, const double* host_coef, double sign, const T* const* V,
+           T* w, size_t n) {
+  SK_REQUIRE(k >= 1 && k <= kMaxBasis, STOKES_ERR_ARG, "maxpy: bad count");
+  if (!n) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * n * (k + 2.0));
+  MultiArgs<T> a{};
+  for (int i = 0; i < k; ++i) {
+    a.v[i] = V[i];
+    a.c[i] = host_coef ? host_coef[i] : 0.0;
+  }
+  a.dev = dev_coef;
+  a.k = k;
+  a.sign = sign;
+  a.n = n;
+  a.w = w;
+  const int grid = (int)std::min<long long>(cdiv((long long)n, 256), 8 * 152);  // as the elementwise kernels
+  switch (pow2_at_least(k)) {
+    case 1: k_maxpy<T, 1><<<grid, 256, 0, ex.s>>>(a); break;
+    case 2: k_maxpy<T, 2><<<grid, 256, 0, ex.s>>>(a); break;
+    case 4: k_maxpy<T, 4><<<grid, 256, 0, ex.s>>>(a); break;
+    case 8: k_maxpy<T, 8><<<grid, 256, 0, ex.s>>>(a); break;
+    case 16: k_maxpy<T, 16><<<grid, 256, 0, ex.s>>>(a); break;
+    default: k_maxpy<T, 32><<<grid, 256, 0, ex.s>>>(a); break;
+  }
+  SK_CHECK_LAUNCH();
+}
+
 // Elementwise kernels run a grid-stride loop over at most kEwBlocks blocks
 // (8 resident 256-thread blocks per SM): a block's coefficient prologue is paid
 // once per ~8 elements per thread rather than once per 256 elements.
@@ -431,7 +568,9 @@ void scalar_sub(const Exec& ex, double* out, const double* a, const double* b) {
   template void lincomb2<T>(const Exec&, size_t, double, const T*, double, const T*, T*);              \
   template void sub_mean<T>(const Exec&, size_t, const double*, double, T*);                           \
   template void sub_ratio<T>(const Exec&, size_t, const double*, const double*, T*);                   \
-  template void cheb_first<T>(const Exec&, size_t, int, const T*, const T*, double, T*, T*);
+  template void cheb_first<T>(const Exec&, size_t, int, const T*, const T*, double, T*, T*);             \
+  template void mdot<T>(const Exec&, const DotScratch&, int, const T* const*, const T*, size_t, double*);  \
+  template void maxpy<T>(const Exec&, int, const double*, const double*, double, const T* const*, T*, size_t);
 SK_INST1(float)
 SK_INST1(double)
 template void convert<double, float>(const Exec&, size_t, const double*, float*);

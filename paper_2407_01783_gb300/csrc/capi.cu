@@ -234,7 +234,8 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   }
   if (c.opt.format != 1) {
     auto add = [&](Csr& m, int p2, int nn) {
-      if (c.opt.format == 0 && m.rows < kStencilMinRows) return;
+      const int min_rows = c.opt.stencil_min_rows > 0 ? c.opt.stencil_min_rows : kStencilMinRows;
+      if ((c.opt.format == 0 || c.opt.format == 3) && m.rows < min_rows) return;
       c.stencils.emplace_back(stencil_from_csr(c.ex, c.arena, st, p2, nn, m));
       m.st = c.stencils.back().get();
     };
@@ -256,7 +257,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     c.A.sym_products = c.opt.format != 3;
   }
   // per-block partials of dot products fused into other kernels
-  c.ds.fused_cap = std::max(std::max(2048, bsr3_dot_grid(c.A)), c.symA ? sym3_grid(*c.symA) : 0);
+  c.ds.fused_cap = std::max(std::max(kDotBlocks * kMaxBasis, bsr3_dot_grid(c.A)), c.symA ? sym3_grid(*c.symA) : 0);
   c.ds.fused_partial = c.arena.alloc<double>(c.ds.fused_cap);
   c.ds.fused_counter = c.arena.alloc<unsigned>(1);
   SK_CUDA(cudaMemsetAsync(c.ds.fused_counter, 0, sizeof(unsigned), c.ex.s));
@@ -295,6 +296,8 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
     c.MQ1_sum = 0;
     for (double x : h) c.MQ1_sum += x;
   }
+  c.tet_vol = c.arena.alloc<double>(6 * (size_t)n * n * n);
+  tet_volumes(c.ex, n, L0.X, c.tet_vol);
   c.U_last = c.arena.alloc<double>(3 * (size_t)L0.nvi);
   c.P_last = c.arena.alloc<double>(L0.np);
   if (c.mixed) {
@@ -350,7 +353,10 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   tune(c.A, 3, 1);
   // threads per row of the symmetric A products: one (measured fastest inside
   // the solve at 48^3: 201 us against 232, 318, 508 us for 2, 4, 8) unless set
-  if (c.A.sym) c.symA->group = c.opt.spmv_group > 0 ? std::min(8, c.A.group) : 1;
+  if (c.A.sym) {
+    c.symA->group = c.opt.spmv_group > 0 ? std::min(8, c.A.group) : 1;
+    c.symA->batch = c.opt.sym_batch > 0 ? c.opt.sym_batch : 8;
+  }
   tune(c.B, 1, 2);
   tune(c.Bt, 3, 3);
   tune(c.MQ, 1, 0);
@@ -423,6 +429,8 @@ void stokes_default_options(stokes_options* o) {
   o->pass_schedule = 0;
   o->cheb_low = 0.1;
   o->cheb_high = 1.1;
+  o->sym_batch = 0;
+  o->stencil_min_rows = 0;
 }
 
 const char* stokes_status_string(int s) {
@@ -460,7 +468,8 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
       !(c->opt.pass_tol > 0 && c->opt.pass_tol < 1) || c->opt.vel_prec < 1 || c->opt.vel_prec > 3 ||
       c->opt.schur_prec < 0 || c->opt.schur_prec > 2 || c->opt.mass_steps_v < 1 ||
       c->opt.pass_schedule < 0 || c->opt.pass_schedule > 2 || !(c->opt.cheb_low > 0) ||
-      !(c->opt.cheb_high > c->opt.cheb_low) || !std::isfinite(c->opt.cheb_high)) {
+      !(c->opt.cheb_high > c->opt.cheb_low) || !std::isfinite(c->opt.cheb_high) ||
+      !(c->opt.sym_batch == 0 || c->opt.sym_batch == 2 || c->opt.sym_batch == 4 || c->opt.sym_batch == 8)) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;

@@ -220,6 +220,7 @@ struct Sym3Op {
   signed char ldel[kMaxSym][3] = {};  // position of j in its class minus position of i in its class
   long long total = 0;                // stored values (9 per stored block)
   int group = 1;                      // threads per row of the products (1, 2, 4 or 8)
+  int batch = 8;                      // entries whose loads a lane issues together (2, 4 or 8)
   double* v64 = nullptr;
   float* v32 = nullptr;
   float* v32lo = nullptr;             // FP32(v64 - v32): double-float residual
@@ -405,6 +406,11 @@ struct AssemblyOut {
 long long assemble(const Exec& ex, int n, const double* X, double mu, double dt,
                    double eps, const Csr& p2, const Csr& p1, const Csr* b, const Csr* bt,
                    const AssemblyOut& out, int* d_bad);
+// |K| per tetrahedron (index 6 * cube + p) of an n^3 Kuhn mesh
+void tet_volumes(const Exec& ex, int n, const double* X, double* vol);
+// F = M_V f from precomputed tet volumes (vol non-null; else as below)
+void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat, const double* f_all, double* F,
+                   const double* vol);
 void assemble_load(const Exec& ex, int n, const double* X, const Csr& p2pat,
                    const double* f_all, double* F);
 // out = M_V^T lu on all P2 nodes (lu on interior nodes, 3 components)
@@ -543,6 +549,14 @@ template <class T> void dots(const Exec& ex, const DotScratch& ds, int k, const 
 template <class T> void axpby(const Exec& ex, size_t n, Coef a, const T* x, Coef b, T* y);
 // x += a d; r -= a q   (a from device scalars)
 template <class T> void cg_update(const Exec& ex, size_t n, Coef a, const T* d, T* x, const T* q, T* r);
+// Arnoldi helpers (up to kMaxBasis vectors per call): out[i] = V_i . w (FP64
+// accumulation, fixed order, w read once), and w += sign * sum_i h_i V_i with
+// h from device scalars (dev_coef) or host constants (host_coef)
+constexpr int kMaxBasis = 32;
+template <class T> void mdot(const Exec& ex, const DotScratch& ds, int k, const T* const* V, const T* w, size_t n,
+                             double* out);
+template <class T> void maxpy(const Exec& ex, int k, const double* dev_coef, const double* host_coef, double sign,
+                              const T* const* V, T* w, size_t n);
 // x += a d; r -= a q; *rr = r . r of the updated r (one kernel)
 template <class T> void cg_update_rr(const Exec& ex, const DotScratch& ds, size_t n, Coef a, const T* d, T* x,
                                      const T* q, T* r, double* rr);
@@ -584,6 +598,7 @@ struct stokes_ctx {
   std::vector<sk::Level> lv;
   sk::Csr A, B, Bt, MQ, LQ;  // fine level (P2P2 BSR3, P1P2, P2P1, P1P1, P1P1)
   double* lumped = nullptr;  // Lambda_V per interior node
+  double* tet_vol = nullptr; // |K| of every tetrahedron of the finest mesh (6 per cube)
   sk::Csr MV;                // scalar P2 mass (C_lambda only); M_V = MV per component
   double* MV_dinv64 = nullptr;
   float* MV_dinv32 = nullptr;

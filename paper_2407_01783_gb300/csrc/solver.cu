@@ -809,18 +809,22 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
         op_A<T>(c, zj, w);
         bt_apply<T>(c.ex, c.Bt, zj + nv, w, (const T*)nullptr, w, -1.0);
         b_apply<T>(c.ex, c.B, zj, w + nv, (const T*)nullptr, 1.0);
-        // CGS2: two passes of h = V^T w, w -= V h
+        // CGS2: two passes of h = V^T w (all basis vectors in one sweep that
+        // reads w once), w -= V h (one sweep)
         for (int pass = 0; pass < 2; ++pass) {
-          for (int i = 0; i <= j; i += kMaxDots) {
-            int k = std::min(kMaxDots, j + 1 - i);
-            const T* xs[kMaxDots];
-            const T* ys[kMaxDots];
-            for (int t = 0; t < k; ++t) xs[t] = *V[i + t], ys[t] = w;
-            dots<T>(c.ex, c.ds, k, xs, ys, N, D + 2 + (pass ? m + 1 : 0) + i, kDotExact);
+          double* h = D + 2 + (pass ? m + 1 : 0);
+          for (int i = 0; i <= j; i += kMaxBasis) {
+            const int k = std::min(kMaxBasis, j + 1 - i);
+            const T* vs[kMaxBasis];
+            for (int t = 0; t < k; ++t) vs[t] = *V[i + t];
+            mdot<T>(c.ex, c.ds, k, vs, w, N, h + i);
           }
-          for (int i = 0; i <= j; ++i)
-            axpby<T>(c.ex, N, Coef::ratio(D + 2 + (pass ? m + 1 : 0) + i, nullptr, -1.0), *V[i],
-                     Coef::constant(1.0), w);
+          for (int i = 0; i <= j; i += kMaxBasis) {
+            const int k = std::min(kMaxBasis, j + 1 - i);
+            const T* vs[kMaxBasis];
+            for (int t = 0; t < k; ++t) vs[t] = *V[i + t];
+            maxpy<T>(c.ex, k, h + i, nullptr, -1.0, vs, w, N);
+          }
         }
         dot1<T>(c, (const T*)w, (const T*)w, N, D + 1, kDotExact);
         SK_CUDA(cudaMemcpyAsync(S.h + s + 1, D + 1, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost,
@@ -859,9 +863,13 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
         for (int k = i + 1; k < j; ++k) t -= H[i * m + k] * y[k];
         y[i] = t / H[i * m + i];
       }
-      for (int i = 0; i < j; ++i) {
-        cg_update<T>(c.ex, nv, Coef::constant(y[i]), (const T*)*Z[i], dU, (const T*)nullptr, (T*)nullptr);
-        cg_update<T>(c.ex, np, Coef::constant(y[i]), (const T*)(*Z[i] + nv), dP, (const T*)nullptr, (T*)nullptr);
+      for (int i = 0; i < j; i += kMaxBasis) {  // [dU; dP] += Z y
+        const int k = std::min(kMaxBasis, j - i);
+        const T* zu[kMaxBasis];
+        const T* zp[kMaxBasis];
+        for (int t = 0; t < k; ++t) zu[t] = *Z[i + t], zp[t] = *Z[i + t] + nv;
+        maxpy<T>(c.ex, k, nullptr, y.data() + i, 1.0, zu, dU, nv);
+        maxpy<T>(c.ex, k, nullptr, y.data() + i, 1.0, zp, dP, np);
       }
       if (done || total >= c.opt.max_outer) break;
       // restart: r = [F; rg] - K x
@@ -1044,7 +1052,7 @@ int solve_context(stokes_ctx* cp, const double* f, const double* g, double tol, 
   auto t0 = std::chrono::steady_clock::now();
   const size_t nv = nvel(c), np = npres(c);
   Tmp<double> F(c.pool, nv);
-  assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, f, F);
+  assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, f, F, c.tet_vol);
   int status = solve_reduced(c, F, g, tol, c.U_last, c.P_last, info, t0);
   expand_velocity(c.ex, c.n, c.U_last, u);
   copy<double>(c, p, (const double*)c.P_last, np);
@@ -1090,7 +1098,7 @@ int adjoint_context(stokes_ctx* cp, const double* dJdu, const double* dJdp, doub
     Tmp<double> Uall(c.pool, 3 * N);
     bsr3_apply<double>(c.ex, c.A, c.U_last, AU, (const double*)nullptr);
     expand_velocity(c.ex, c.n, c.U_last, Uall);
-    assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, Uall, MU);
+    assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, Uall, MU, c.tet_vol);
     lincomb2<double>(c.ex, nv, 1.0 / c.mu, AU, -1.0 / (c.mu * c.dt), MU, AU);  // E_V U
     const int s = c.sc.take(1);
     dot1<double>(c, (const double*)lu, (const double*)AU, nv, c.sc.d + s);
@@ -1160,7 +1168,7 @@ void apply_operator(stokes_ctx* cp, int op, int level, const double* x, double* 
       SK_REQUIRE(level + 1 < (int)c.lv.size(), STOKES_ERR_ARG, "no coarser level");
       spmv_store<double>(c.ex, L.P1, 1, x, y, STOKES_KERNEL_TRANSFER);
       break;
-    case STOKES_OP_LOAD: assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, x, y); break;
+    case STOKES_OP_LOAD: assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, x, y, c.tet_vol); break;
     case STOKES_OP_A_DF: {
       SK_REQUIRE(c.A.v32lo, STOKES_ERR_ARG, "double-float A needs a mixed-precision context");
       Tmp<float> xh(c.pool, nv), xl(c.pool, nv);

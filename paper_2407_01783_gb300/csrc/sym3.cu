@@ -115,11 +115,11 @@ struct SymBatch {
   static constexpr int U = 8 / G;
 };
 
-// this lane's share of acc[r] = sum over the row's blocks of A(i, j)_{r q} x_j[q]
-template <int G, class T>
+// this lane's share of acc[r] = sum over the row's blocks of A(i, j)_{r q} x_j[q],
+// U entries' loads in flight per lane
+template <int G, int U, class T>
 __device__ __forceinline__ void sym3_row(const Sym3Args& a, const SymRow& R, int lane, const T* __restrict__ v,
                                          const T* __restrict__ x, size_t xs, T acc[3]) {
-  constexpr int U = SymBatch<G>::U;
   const int c = R.c;
   const int last = (int)xs - 1;
   const size_t rc = (size_t)a.prows[c];
@@ -184,7 +184,7 @@ __device__ __forceinline__ void sym3_row(const Sym3Args& a, const SymRow& R, int
 // Blocks walk the virtual blocks (plane order) with a grid stride; the dot
 // variant runs one resident wave so that its grid sum takes one counter
 // increment per resident block.
-template <int G, class T, bool DOT>
+template <int G, int U, class T, bool DOT>
 __global__ void __launch_bounds__(kSymBlock) k_sym3(const Sym3Args a, int nvb, const T* __restrict__ v,
                                                    const T* __restrict__ x, size_t xs, const T* __restrict__ b,
                                                    T* __restrict__ y, double* partial, unsigned* counter,
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kSymBlock) k_sym3(const Sym3Args a, int nvb, c
   for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
     const SymRow R = sym3_locate<G>(a, vb);
     T acc[3] = {T(0), T(0), T(0)};
-    if (R.valid) sym3_row<G, T>(a, R, lane, v, x, xs, acc);
+    if (R.valid) sym3_row<G, U, T>(a, R, lane, v, x, xs, acc);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1)
 #pragma unroll
@@ -312,7 +312,7 @@ double sym3_bytes(const Sym3Op& so, int esz, int rows, int streams) {
   return (double)so.total * esz + (double)esz * 3.0 * rows * (1 + streams);
 }
 
-template <int G, class T>
+template <int G, int U, class T>
 static void sym3_launch_g(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, const DotScratch* ds,
                           double* dot) {
   const Sym3Op& so = *m.sym;
@@ -327,17 +327,17 @@ static void sym3_launch_g(const Exec& ex, const Csr& m, const T* x, T* y, const 
     int dev = 0, sms = 0, occ = 0;
     SK_CUDA(cudaGetDevice(&dev));
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (dot) SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym3<G, T, true>, kSymBlock, 0));
-    else SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym3<G, T, false>, kSymBlock, 0));
+    if (dot) SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym3<G, U, T, true>, kSymBlock, 0));
+    else SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym3<G, U, T, false>, kSymBlock, 0));
     w = std::max(1, sms * std::max(1, occ));
   }
   const int grid = std::min(nvb, w);
   if (dot) {
     SK_REQUIRE(ds && ds->fused_partial && grid <= ds->fused_cap, STOKES_ERR_ARG, "fused dot scratch too small");
-    k_sym3<G, T, true><<<grid, kSymBlock, 0, ex.s>>>(a, nvb, so.template v<T>(), x, (size_t)m.rows, b, y,
+    k_sym3<G, U, T, true><<<grid, kSymBlock, 0, ex.s>>>(a, nvb, so.template v<T>(), x, (size_t)m.rows, b, y,
                                                     ds->fused_partial, ds->fused_counter, dot);
   } else {
-    k_sym3<G, T, false><<<grid, kSymBlock, 0, ex.s>>>(a, nvb, so.template v<T>(), x, (size_t)m.rows, b, y, nullptr,
+    k_sym3<G, U, T, false><<<grid, kSymBlock, 0, ex.s>>>(a, nvb, so.template v<T>(), x, (size_t)m.rows, b, y, nullptr,
                                                      nullptr, nullptr);
   }
   SK_CHECK_LAUNCH();
@@ -345,12 +345,15 @@ static void sym3_launch_g(const Exec& ex, const Csr& m, const T* x, T* y, const 
 
 template <class T>
 void sym3_launch(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, const DotScratch* ds, double* dot) {
-  switch (m.sym->group) {
-    case 1: sym3_launch_g<1, T>(ex, m, x, y, b, ds, dot); break;
-    case 2: sym3_launch_g<2, T>(ex, m, x, y, b, ds, dot); break;
-    case 8: sym3_launch_g<8, T>(ex, m, x, y, b, ds, dot); break;
-    default: sym3_launch_g<4, T>(ex, m, x, y, b, ds, dot); break;
-  }
+  // (threads per row, entries in flight per lane)
+  const int g = m.sym->group, u = m.sym->batch;
+  if (g == 1 && u == 2) sym3_launch_g<1, 2, T>(ex, m, x, y, b, ds, dot);
+  else if (g == 1 && u == 4) sym3_launch_g<1, 4, T>(ex, m, x, y, b, ds, dot);
+  else if (g == 1) sym3_launch_g<1, 8, T>(ex, m, x, y, b, ds, dot);
+  else if (g == 2 && u == 2) sym3_launch_g<2, 2, T>(ex, m, x, y, b, ds, dot);
+  else if (g == 2) sym3_launch_g<2, 4, T>(ex, m, x, y, b, ds, dot);
+  else if (g == 4) sym3_launch_g<4, 2, T>(ex, m, x, y, b, ds, dot);
+  else sym3_launch_g<8, 1, T>(ex, m, x, y, b, ds, dot);
 }
 
 template <int G>
