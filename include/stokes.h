@@ -158,6 +158,11 @@ typedef struct {
                             default 8) */
   int stencil_min_rows;  /* formats 0 and 3: levels with at least this many rows
                             use stencil storage (0: 2^18) */
+  int host_wait;         /* how the host thread waits for the device scalars
+                            it reads: 0 spins (lowest latency; the default),
+                            1 sleeps until the GPU signals (blocking-sync
+                            events: the better choice when more solver threads
+                            than host cores wait at once, as in a batch) */
 } stokes_options;
 
 typedef struct {
@@ -191,6 +196,22 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt,
  * int p_h = 0. info may be NULL. */
 stokes_status stokes_solve(stokes_ctx* ctx, const double* f, const double* g,
                            double tol, double* u, double* p, stokes_info* info);
+
+/* k systems with the same operator (Eq. Saddle_point_A_BT_B, k right-hand
+ * sides): f device [k][(2n+1)^3][3], g device [k][(n+1)^3] or NULL, u device
+ * [k][(2n+1)^3][3], p device [k][(n+1)^3], info NULL or an array of k. With
+ * Method 2 the systems are solved four at a time in lockstep (FGMRES of Sec.
+ * 2.4 per system, each with its own Krylov basis, Hessenberg matrix and
+ * convergence test): every V-cycle, Chebyshev mass inverse and vector kernel
+ * sweeps its matrix and launches once for the four systems. A last group of
+ * two or three systems is padded with zero systems, a single one takes the
+ * stokes_solve path; Method 1 solves the systems one after another. Each
+ * system meets tol on its own full residual (info[i].rel_residual);
+ * info[i].outer_iters counts the iterations system i took part in. Returns
+ * STOKES_OK if every system converged, else the first failing status. A
+ * following stokes_adjoint uses the last system's solution. 1 <= k <= 4096. */
+stokes_status stokes_solve_multi(stokes_ctx* ctx, int k, const double* f, const double* g,
+                                 double tol, double* u, double* p, stokes_info* info);
 
 /* Same as stokes_solve with HOST arrays; the host<->device copies are part
  * of the call. */

@@ -24,6 +24,7 @@ from ._lib import (KERNEL, MAT, METHOD_COUPLED, METHOD_SCHUR, OP, PRECISION_FP64
                    StokesOptions)
 
 __all__ = ["StokesError", "StokesOptions", "StokesInfo", "Stokes", "StokesBatch", "stokes_default_options",
+           "stokes_solve_multi",
            "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_adjoint",
            "stokes_destroy", "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_export", "stokes_sizes",
            "stokes_kernel_stats", "stokes_kernel_timing", "stokes_kernel_stats_reset", "stokes_profile_mode",
@@ -96,6 +97,17 @@ def stokes_solve(ctx, f: torch.Tensor, g: torch.Tensor | None, tol: float, u: to
     _check(_L.stokes_solve(ctx, _ptr(f), _ptr(g), tol, _ptr(u), _ptr(p), C.byref(info)),
            "stokes_solve", allow=(-4,) if allow_not_converged else ())
     return info
+
+
+def stokes_solve_multi(ctx, f: torch.Tensor, g: torch.Tensor | None, tol: float, u: torch.Tensor,
+                       p: torch.Tensor, allow_not_converged: bool = False) -> list:
+    """k systems with one operator: f [k, (2n+1)^3, 3], g [k, (n+1)^3] or None,
+    u like f, p [k, (n+1)^3] (all device, FP64, contiguous). Returns k infos."""
+    k = int(f.shape[0])
+    infos = (StokesInfo * k)()
+    _check(_L.stokes_solve_multi(ctx, k, _ptr(f), _ptr(g), tol, _ptr(u), _ptr(p), infos),
+           "stokes_solve_multi", allow=(-4,) if allow_not_converged else ())
+    return list(infos)
 
 
 def stokes_solve_host(ctx, f: np.ndarray, g: np.ndarray | None, tol: float, u: np.ndarray,
@@ -233,6 +245,22 @@ class Stokes:
         info = stokes_solve(self.ctx, f, g, tol, u, p, allow_not_converged)
         return u, p, info
 
+    def solve_multi(self, F: torch.Tensor, G: torch.Tensor | None = None, tol: float = 1e-8,
+                    out=None, allow_not_converged=False):
+        """k right-hand sides at once: F [k, (2n+1)^3, 3], G [k, (n+1)^3] or
+        None. Returns (U [k, (2n+1)^3, 3], P [k, (n+1)^3], infos)."""
+        F = F.to(self.device, torch.float64).contiguous().reshape(-1, self.n_p2, 3)
+        k = F.shape[0]
+        if G is not None:
+            G = G.to(self.device, torch.float64).contiguous().reshape(k, self.n_p1)
+        if out is None:
+            U = torch.empty_like(F)
+            P = torch.empty(k, self.n_p1, dtype=torch.float64, device=self.device)
+        else:
+            U, P = out
+        infos = stokes_solve_multi(self.ctx, F, G, tol, U, P, allow_not_converged)
+        return U, P, infos
+
     def solve_host(self, f: np.ndarray, g: np.ndarray | None = None, tol: float = 1e-8):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.n_p2, 3)
         u = np.empty_like(f)
@@ -269,11 +297,19 @@ class StokesBatch:
     Each instance has its own context and CUDA stream; ``solve_all`` issues
     every instance's right-hand sides from its own host thread (the C calls
     release the GIL), so the kernels of all instances overlap on the GPU.
+    With ``multi`` (the default) an instance's right-hand sides go through one
+    ``stokes_solve_multi`` call (Method 2: four systems in lockstep, every
+    matrix sweep shared); otherwise they are solved one after another.
     """
 
     def __init__(self, instances, options: StokesOptions | None = None,
-                 device: str | torch.device = "cuda"):
+                 device: str | torch.device = "cuda", multi: bool = True, host_wait: int | None = None):
         self.device = torch.device(device)
+        self.multi = multi
+        options = StokesOptions.from_buffer_copy(options) if options is not None else stokes_default_options()
+        # many solver threads waiting at once: sleep on blocking-sync events
+        # rather than spin (unless the caller chose)
+        options.host_wait = host_wait if host_wait is not None else (1 if len(instances) > 1 else options.host_wait)
         self.solvers = []
         for (n, vertices, mu, dt, gamma) in instances:
             st = torch.cuda.Stream(self.device)
@@ -287,13 +323,27 @@ class StokesBatch:
     def dofs(self):
         return [S.sizes["dofs"] for S in self.solvers]
 
+    def stack(self, forces):
+        """forces[i] (a list of [(2n_i+1)^3, 3] tensors, or one [k, (2n_i+1)^3, 3]
+        tensor) -> one contiguous FP64 device tensor per instance."""
+        out = []
+        for S, fl in zip(self.solvers, forces):
+            F = fl if isinstance(fl, torch.Tensor) else torch.stack([f.reshape(S.n_p2, 3) for f in fl])
+            out.append(F.to(self.device, torch.float64).contiguous())
+        return out
+
     def solve_all(self, forces, tol: float = 1e-8, outs=None):
-        """forces[i]: list of device tensors [(2n_i+1)^3, 3] for instance i.
-        Returns (outs, infos, device_ms): outs[i][k] = (u, p)."""
+        """forces[i]: list of device tensors [(2n_i+1)^3, 3] (or one stacked
+        [k, (2n_i+1)^3, 3] tensor) for instance i. Returns (outs, infos,
+        device_ms): outs[i][k] = (u, p)."""
         import concurrent.futures as cf
+        F = self.stack(forces)
         if outs is None:
-            outs = [[(torch.empty_like(f), torch.empty(S.n_p1, dtype=torch.float64, device=self.device))
-                     for f in fl] for S, fl in zip(self.solvers, forces)]
+            outs = []
+            for S, Fi in zip(self.solvers, F):
+                U = torch.empty_like(Fi)
+                P = torch.empty(Fi.shape[0], S.n_p1, dtype=torch.float64, device=self.device)
+                outs.append([(U[k], P[k]) for k in range(Fi.shape[0])])
         start = torch.cuda.Event(enable_timing=True)
         ends = [torch.cuda.Event(enable_timing=True) for _ in self.solvers]
         launch = torch.cuda.current_stream(self.device)
@@ -304,9 +354,16 @@ class StokesBatch:
 
         def run(i):
             S = self.solvers[i]
-            res = []
-            for f, (u, p) in zip(forces[i], outs[i]):
-                res.append(stokes_solve(S.ctx, f, None, tol, u, p).as_dict())
+            u0, p0 = outs[i][0]
+            k = len(outs[i])
+            stacked = (all(u.data_ptr() == u0.data_ptr() + j * u0.numel() * 8 for j, (u, _) in enumerate(outs[i]))
+                       and all(p.data_ptr() == p0.data_ptr() + j * p0.numel() * 8 for j, (_, p) in enumerate(outs[i])))
+            if self.multi and stacked:
+                U = torch.as_strided(u0, (k, S.n_p2, 3), (S.n_p2 * 3, 3, 1))
+                P = torch.as_strided(p0, (k, S.n_p1), (S.n_p1, 1))
+                res = [x.as_dict() for x in stokes_solve_multi(S.ctx, F[i], None, tol, U, P)]
+            else:
+                res = [stokes_solve(S.ctx, F[i][j], None, tol, u, p).as_dict() for j, (u, p) in enumerate(outs[i])]
             ends[i].record(S.stream)
             infos[i] = res
 

@@ -42,6 +42,7 @@ class StokesOptions(C.Structure):
         ("coarse_kernel", C.c_int), ("pass_schedule", C.c_int),
         ("cheb_low", C.c_double), ("cheb_high", C.c_double), ("sym_batch", C.c_int),
         ("stencil_min_rows", C.c_int),
+        ("host_wait", C.c_int),
     ]
 
     def as_dict(self):
@@ -79,6 +80,8 @@ def load() -> C.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = [vp, vp, vp, C.c_double, vp, vp, C.POINTER(StokesInfo)]
         fn.restype = C.c_int
+    lib.stokes_solve_multi.argtypes = [vp, C.c_int, vp, vp, C.c_double, vp, vp, C.POINTER(StokesInfo)]
+    lib.stokes_solve_multi.restype = C.c_int
     lib.stokes_adjoint.argtypes = [vp, vp, vp, C.c_double, vp, vp, dp, C.POINTER(StokesInfo)]
     lib.stokes_adjoint.restype = C.c_int
     lib.stokes_destroy.argtypes = [vp]
@@ -115,7 +118,7 @@ def load() -> C.CDLL:
 
 
 # names declared in include/stokes.h (checked by the CPU test suite)
-EXPORTS = ["stokes_default_options", "stokes_setup", "stokes_solve", "stokes_solve_host",
+EXPORTS = ["stokes_default_options", "stokes_setup", "stokes_solve", "stokes_solve_host", "stokes_solve_multi",
            "stokes_adjoint", "stokes_destroy", "stokes_status_string", "stokes_last_error",
            "stokes_apply", "stokes_apply_agamma_noalloc", "stokes_matrix_shape", "stokes_matrix_export", "stokes_sizes",
            "stokes_kernel_stats", "stokes_kernel_timing", "stokes_kernel_stats_reset", "stokes_profile_mode",

@@ -128,7 +128,7 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   c.prof.only = c.opt.profile >= 2 ? c.opt.profile - 2 : -1;
   c.pool.arena = &c.arena;
   c.mixed = c.opt.precision == STOKES_PRECISION_MIXED;
-  c.sc.cap = 1024;
+  c.sc.cap = 4096;
   c.sc.d = c.arena.alloc<double>(c.sc.cap);
   SK_CUDA(cudaMallocHost(&c.sc.h, sizeof(double) * c.sc.cap));
   c.ds.partial = c.arena.alloc<double>((size_t)kMaxDots * kDotBlocks);
@@ -136,7 +136,9 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   SK_CUDA(cudaMemsetAsync(c.ds.counter, 0, sizeof(unsigned), c.ex.s));
   c.d_flag = c.arena.alloc<int>(1);
   c.ex.flag = c.d_flag;
-  SK_CUDA(cudaEventCreateWithFlags(&c.ev_read, cudaEventDisableTiming));
+  const unsigned evf = cudaEventDisableTiming | (c.opt.host_wait ? cudaEventBlockingSync : 0u);
+  SK_CUDA(cudaEventCreateWithFlags(&c.ev_read, evf));
+  SK_CUDA(cudaEventCreateWithFlags(&c.ev_sync, evf));
 
   // level sizes n -> ceil(n/2) -> ... down to at most 3 cubes per side (nested
   // Kuhn meshes when n is even, logical-coordinate transfers otherwise)
@@ -261,6 +263,10 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   c.ds.fused_partial = c.arena.alloc<double>(c.ds.fused_cap);
   c.ds.fused_counter = c.arena.alloc<unsigned>(1);
   SK_CUDA(cudaMemsetAsync(c.ds.fused_counter, 0, sizeof(unsigned), c.ex.s));
+  c.ds.k_cap = kdot_scratch(3 * (size_t)c.lv[0].nvi + c.lv[0].np, kMaxRhs);
+  c.ds.k_partial = c.arena.alloc<double>((size_t)c.ds.k_cap);
+  c.ds.k_counter = c.arena.alloc<unsigned>(kMaxRhs);
+  SK_CUDA(cudaMemsetAsync(c.ds.k_counter, 0, sizeof(unsigned) * kMaxRhs, c.ex.s));
   clock.mark(STOKES_SETUP_STORAGE);
   Level& Lc = c.lv.back();
   coarse_inverse(c, Lc.A3, &Lc.A3_cinv64);
@@ -431,6 +437,7 @@ void stokes_default_options(stokes_options* o) {
   o->cheb_high = 1.1;
   o->sym_batch = 0;
   o->stencil_min_rows = 0;
+  o->host_wait = 0;
 }
 
 const char* stokes_status_string(int s) {
@@ -469,7 +476,8 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
       c->opt.schur_prec < 0 || c->opt.schur_prec > 2 || c->opt.mass_steps_v < 1 ||
       c->opt.pass_schedule < 0 || c->opt.pass_schedule > 2 || !(c->opt.cheb_low > 0) ||
       !(c->opt.cheb_high > c->opt.cheb_low) || !std::isfinite(c->opt.cheb_high) ||
-      !(c->opt.sym_batch == 0 || c->opt.sym_batch == 2 || c->opt.sym_batch == 4 || c->opt.sym_batch == 8)) {
+      !(c->opt.sym_batch == 0 || c->opt.sym_batch == 2 || c->opt.sym_batch == 4 || c->opt.sym_batch == 8) ||
+      c->opt.host_wait < 0 || c->opt.host_wait > 1) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;
@@ -500,6 +508,24 @@ stokes_status stokes_solve(stokes_ctx* c, const double* f, const double* g, doub
   int st = guarded([&]() { status = solve_context(c, f, g, tol, u, p, info); });
   if (st != STOKES_OK) {
     if (info) info->status = st;
+    return (stokes_status)st;
+  }
+  if (status != STOKES_OK) g_last_error = stokes_status_string(status);
+  return (stokes_status)status;
+}
+
+stokes_status stokes_solve_multi(stokes_ctx* c, int k, const double* f, const double* g, double tol, double* u,
+                                 double* p, stokes_info* info) {
+  g_last_error.clear();
+  if (!c || !f || !u || !p || !(tol > 0) || k < 1 || k > 4096) {
+    g_last_error = "stokes_solve_multi: null argument, tol <= 0 or k outside [1, 4096]";
+    return STOKES_ERR_ARG;
+  }
+  int status = STOKES_OK;
+  int st = guarded([&]() { status = solve_multi_context(c, k, f, g, tol, u, p, info); });
+  if (st != STOKES_OK) {
+    if (info)
+      for (int i = 0; i < k; ++i) info[i].status = st;
     return (stokes_status)st;
   }
   if (status != STOKES_OK) g_last_error = stokes_status_string(status);
@@ -564,6 +590,7 @@ stokes_status stokes_destroy(stokes_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->prof.reset();
   if (c->ev_read) cudaEventDestroy(c->ev_read);
+  if (c->ev_sync) cudaEventDestroy(c->ev_sync);
   if (c->sc.h) cudaFreeHost(c->sc.h);
   c->arena.free_all();
   delete c;

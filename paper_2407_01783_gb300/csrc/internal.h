@@ -478,6 +478,11 @@ struct DotScratch {
   double* fused_partial = nullptr;
   unsigned* fused_counter = nullptr;
   int fused_cap = 0;
+  // dot products of K right-hand sides (multi.cu): partials [K][vectors][blocks]
+  // and one completion counter per (right-hand side, vector)
+  double* k_partial = nullptr;
+  unsigned* k_counter = nullptr;
+  long long k_cap = 0;
 };
 
 #ifdef __CUDACC__
@@ -575,6 +580,93 @@ template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D
 // hi = FP32(x), lo = FP32(x - hi)
 void split_f64(const Exec& ex, size_t n, const double* x, float* hi, float* lo);
 template <class S, class D> void add_convert(const Exec& ex, size_t n, const S* x, D* y);
+
+// ---------------------------------------------------------------------------
+// K right-hand sides in lockstep (multi.cu). A K-vector stores K systems'
+// reduced unknowns as the velocity blocks [K][nu] followed by the pressure
+// blocks [K][np]; `parts` selects the velocity (1), pressure (2) or both (3)
+// parts of each right-hand side's segment. Vectors of K plain blocks of
+// length n are K-vectors with nu = n, np = 0, parts = 1.
+// ---------------------------------------------------------------------------
+constexpr int kMaxRhs = 8;
+constexpr int kMaxBasisK = 32;
+// Per-right-hand-side coefficient: value(k) = c[k] + s * num[k*stride] /
+// den[k*stride] (device scalars; null num: c[k] alone), 0 for a right-hand
+// side whose bit in `active` is clear. `positive`: as Coef::cg_ratio.
+struct KCoefs {
+  double c[kMaxRhs] = {};
+  double s = 0;
+  const double* num = nullptr;
+  const double* den = nullptr;
+  int stride = 1;
+  int positive = 0;
+  unsigned active = ~0u;
+  static KCoefs constant(double v) {
+    KCoefs k;
+    for (int i = 0; i < kMaxRhs; ++i) k.c[i] = v;
+    return k;
+  }
+  static KCoefs host(const double* v, int K) {
+    KCoefs k;
+    for (int i = 0; i < K; ++i) k.c[i] = v[i];
+    return k;
+  }
+  static KCoefs ratio(const double* num, const double* den, double s = 1.0, int stride = 1) {
+    KCoefs k;
+    k.s = s;
+    k.num = num;
+    k.den = den;
+    k.stride = stride;
+    return k;
+  }
+  static KCoefs cg_ratio(const double* num, const double* den, double s = 1.0, int stride = 1) {
+    KCoefs k = ratio(num, den, s, stride);
+    k.positive = 1;
+    return k;
+  }
+  KCoefs& mask(unsigned m) {
+    active = m;
+    return *this;
+  }
+#ifdef __CUDACC__
+  __device__ double value(int k, int* flag) const {
+    if (!((active >> k) & 1u)) return 0.0;
+    double v = c[k];
+    if (num) {
+      const double dn = den ? den[(size_t)k * stride] : 1.0;
+      if (positive && !(dn > 0.0)) {
+        if (flag) atomicOr(flag, 1);
+        return v;
+      }
+      if (dn != 0.0) v += s * num[(size_t)k * stride] / dn;
+    }
+    return v;
+  }
+#endif
+};
+template <class T> struct KBasis {
+  const T* v[kMaxBasisK];
+};
+struct KHost {
+  double c[kMaxRhs * kMaxBasisK];
+};
+// out[k] = x_k . y_k over the segment (y null: sum of x_k), FP64 accumulation
+template <class T> void kdot(const Exec& ex, const DotScratch& ds, size_t nu, size_t np, int K, int parts, const T* x,
+                             const T* y, double* out);
+// y_k = a_k x_k + b_k y_k over the segment
+template <class T> void kaxpby(const Exec& ex, size_t nu, size_t np, int K, int parts, const KCoefs& a, const T* x,
+                               const KCoefs& b, T* y);
+// y_k += c_k over the segment
+template <class T> void kaddconst(const Exec& ex, size_t nu, size_t np, int K, int parts, const KCoefs& c, T* y);
+// Arnoldi helpers over whole segments (parts = 3) of J <= kMaxBasisK
+// K-vectors: out[k * ld + i] = V_i(k) . w(k); w(k) += sign * sum_i h_ki V_i(k)
+// with h_ki = h[k * ld + i] (device) or hhost[k * ld + i] (host)
+template <class T> void kmdot(const Exec& ex, const DotScratch& ds, size_t nu, size_t np, int K, int J,
+                              const T* const* V, const T* w, double* out, int ld);
+template <class T> void kmaxpy(const Exec& ex, size_t nu, size_t np, int K, int J, const T* const* V, const double* h,
+                               const double* hhost, int ld, double sign, T* w);
+// scratch doubles the K-dot kernels need (capacity of DotScratch::k_partial)
+long long kdot_scratch(size_t len_max, int K);
 void expand_velocity(const Exec& ex, int n, const double* ured, double* uall);
 void restrict_velocity(const Exec& ex, int n, const double* uall, double* ured);
 void count_nonfinite(const Exec& ex, size_t n, const double* x, int* flag);
@@ -618,6 +710,7 @@ struct stokes_ctx {
   // host staging for *_host calls
   double *f_dev = nullptr, *g_dev = nullptr, *u_dev = nullptr, *p_dev = nullptr;
   cudaEvent_t ev_read = nullptr;  // host reads of device scalars
+  cudaEvent_t ev_sync = nullptr;  // host waits for the stream (blocking-sync with host_wait = 1)
   // levels >= 1 of the V-cycle of A~_3 (which = 0), of eps M_Q + L_Q
   // (which = 1) and of the block operator A~_1 / A~_2 (which = 2), FP64 [0]
   // and FP32 [1]: fixed input/output vectors, a private
@@ -658,6 +751,8 @@ struct stokes_ctx {
 
 namespace sk {
 void setup_context(stokes_ctx* c, int n, const double* Xhost);
+int solve_multi_context(stokes_ctx* c, int k, const double* f, const double* g, double tol, double* u,
+                        double* p, stokes_info* info);
 int solve_context(stokes_ctx* c, const double* f, const double* g, double tol, double* u,
                   double* p, stokes_info* info);
 int adjoint_context(stokes_ctx* c, const double* dJdu, const double* dJdp, double tol,

@@ -35,9 +35,15 @@ template <> inline const float* pick<float>(const double*, const float* b) { ret
 // ---------------------------------------------------------------------------
 // host reads of device scalars
 // ---------------------------------------------------------------------------
+// wait for all work issued on the context's stream (spinning or sleeping, as
+// the event's flags say)
+static void host_sync(stokes_ctx& c) {
+  SK_CUDA(cudaEventRecord(c.ev_sync, c.ex.s));
+  SK_CUDA(cudaEventSynchronize(c.ev_sync));
+}
 static double read_now(stokes_ctx& c, const double* d, int slot) {
   SK_CUDA(cudaMemcpyAsync(c.sc.h + slot, d, sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  host_sync(c);
   return c.sc.h[slot];
 }
 static void read_issue(stokes_ctx& c, const double* d, int slot) {
@@ -108,16 +114,19 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
   if (xa != x) copy<T>(c, x, xa, len);
 }
 
-// M_Q^{-1} b by Chebyshev-Jacobi on the exact Wathen interval
-template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int steps) {
-  cheb_run<T>(c, c.MQ, 1, pick<T>(c.MQ_dinv64, c.MQ_dinv32), kMassLow, kMassHigh, std::max(1, steps), b, x, true,
+// M_Q^{-1} b by Chebyshev-Jacobi on the exact Wathen interval (K right-hand
+// sides [K][np] in one sweep of M_Q)
+template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int steps, int K = 1) {
+  cheb_run<T>(c, c.MQ, K, pick<T>(c.MQ_dinv64, c.MQ_dinv32), kMassLow, kMassHigh, std::max(1, steps), b, x, true,
               STOKES_KERNEL_SPMV_P1);
 }
 
 // ---------------------------------------------------------------------------
-// geometric V-cycle; which = 0: A~_3 on 3 interleaved components, 1: eps M_Q + L_Q
+// geometric V-cycle; which = 0: A~_3 on 3 interleaved components, 1: eps M_Q + L_Q;
+// K right-hand sides: 3K (resp. K) component-major components share every
+// sweep of the level matrices
 // ---------------------------------------------------------------------------
-template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero);
+template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K = 1);
 
 // Levels >= 1 are latency-bound (a few thousand rows per launch), so below
 // level 0 the V-cycle is replayed from a CUDA graph. Graph launches are not
@@ -326,9 +335,10 @@ static void level_resid(stokes_ctx& c, const Csr& M, int nr, const T* b, const T
   else spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
 }
 
-template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero) {
+template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K) {
+  SK_REQUIRE(which != 2 || K == 1, STOKES_ERR_ARG, "block V-cycle: one right-hand side per call");
   Level& L = c.lv[l];
-  const int nr = which == 1 ? 1 : 3;
+  const int nr = (which == 1 ? 1 : 3) * K;
   const Csr& M = level_op(L, which);
   size_t len = (size_t)M.rows * nr;
   if (l + 1 == (int)c.lv.size()) {
@@ -350,7 +360,7 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
   Level& Lc = c.lv[l + 1];
   const Csr& Mc = level_op(Lc, which);
   size_t lenc = (size_t)Mc.rows * nr;
-  if (l == 0 && coarse_kernel_ok(c, which)) {
+  if (l == 0 && K == 1 && coarse_kernel_ok(c, which)) {
     MgProgram* P = mg_program<T>(c, which);
     {
       Tmp<T> r(c.pool, len);
@@ -359,7 +369,7 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
     }
     P->launch(c.ex);
     spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, (const T*)P->x, x, STOKES_KERNEL_TRANSFER);
-  } else if (l == 0 && coarse_graph_ok(c, which)) {
+  } else if (l == 0 && K == 1 && coarse_graph_ok(c, which)) {
     auto& G = c.cgraph[which][std::is_same<T, float>::value ? 1 : 0];
     if (!G.b) {
       G.b = c.arena.raw(lenc * sizeof(T));
@@ -378,21 +388,21 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
     level_resid<T>(c, M, nr, b, x, r, kind);
     Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);
     spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER);
-    vcycle<T>(c, which, l + 1, bc, xc, true);
+    vcycle<T>(c, which, l + 1, bc, xc, true, K);
     spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER);
   }
   cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind);
 }
 
-template <class T> static void vcycles_plain(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
-  vcycle<T>(c, which, 0, b, x, true);
-  for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, b, x, false);
+template <class T> static void vcycles_plain(stokes_ctx& c, int which, const T* b, T* x, int cycles, int K = 1) {
+  vcycle<T>(c, which, 0, b, x, true, K);
+  for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, b, x, false, K);
 }
 
 // A whole V-cycle in one graph needs every launch it makes to be untimed:
 // allowed without profiling, or when the one timed class is not launched by
 // a V-cycle of this kind.
-constexpr size_t kMaxCycleGraphs = 64;
+constexpr size_t kMaxCycleGraphs = 128;
 static bool cycle_graph_ok(const stokes_ctx& c, int which) {
   if (!c.opt.graphs || c.graphs_off || c.in_cycle_graph) return false;
   (void)which;
@@ -472,13 +482,21 @@ template <class Body> static void graph_region(stokes_ctx& c, const GraphKey& ke
     }
 }
 
-template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles) {
-  if (!cycle_graph_ok(c, which)) {
-    vcycles_plain<T>(c, which, b, x, cycles);
+// K right-hand sides: b, x hold K blocks of the cycle's vector length
+// (component-major, so the blocks are the 3K or K components of one sweep)
+template <class T> static void vcycles(stokes_ctx& c, int which, const T* b, T* x, int cycles, int K = 1) {
+  if (which == 2 && K > 1) {  // the 3x3-block operator takes one right-hand side per cycle
+    const size_t len = 3 * (size_t)c.lv[0].nvi;
+    for (int k = 0; k < K; ++k) vcycles<T>(c, which, b + k * len, x + k * len, cycles, 1);
     return;
   }
-  graph_region(c, GraphKey(which, (int)std::is_same<T, float>::value, (const void*)b, (void*)x, cycles),
-               [&]() { vcycles_plain<T>(c, which, b, x, cycles); });
+  if (!cycle_graph_ok(c, which)) {
+    vcycles_plain<T>(c, which, b, x, cycles, K);
+    return;
+  }
+  graph_region(c,
+               GraphKey(which, (int)std::is_same<T, float>::value + 2 * (K - 1), (const void*)b, (void*)x, cycles),
+               [&]() { vcycles_plain<T>(c, which, b, x, cycles, K); });
 }
 
 // ---------------------------------------------------------------------------
@@ -829,7 +847,7 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
         dot1<T>(c, (const T*)w, (const T*)w, N, D + 1, kDotExact);
         SK_CUDA(cudaMemcpyAsync(S.h + s + 1, D + 1, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost,
                                 c.ex.s));
-        SK_CUDA(cudaStreamSynchronize(c.ex.s));
+        host_sync(c);
         double hn = std::sqrt(S.h[s + 1]);
         for (int i = 0; i <= j; ++i) H[i * m + j] = S.h[s + 2 + i] + S.h[s + 2 + m + 1 + i];
         H[(j + 1) * m + j] = hn;
@@ -925,7 +943,7 @@ static void correction(stokes_ctx& c, const double* rF, const double* rg, double
 static int read_flag(stokes_ctx& c) {
   int flag = 0;
   SK_CUDA(cudaMemcpyAsync(&flag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.ex.s));
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  host_sync(c);
   return flag;
 }
 
@@ -948,7 +966,7 @@ static double full_residual(stokes_ctx& c, const double* F, const double* g, con
   dots<double>(c.ex, c.ds, 1, xs, xs, nv, c.sc.d + s);
   dots<double>(c.ex, c.ds, 1, xs + 1, xs + 1, np, c.sc.d + s + 1);
   SK_CUDA(cudaMemcpyAsync(c.sc.h + s, c.sc.d + s, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  host_sync(c);
   double rr = c.sc.h[s] + c.sc.h[s + 1];
   c.sc.give(2);
   return std::sqrt(rr) / normFg;
@@ -977,7 +995,7 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
     const double* fs[1] = {F};
     dots<double>(c.ex, c.ds, 1, fs, fs, nv, c.sc.d + s + 2);
     SK_CUDA(cudaMemcpyAsync(c.sc.h + s, c.sc.d + s, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.ex.s));
-    SK_CUDA(cudaStreamSynchronize(c.ex.s));
+    host_sync(c);
   }
   double gsum = c.sc.h[s], gg = c.sc.h[s + 1], FF = c.sc.h[s + 2];
   c.sc.give(3);
@@ -1050,16 +1068,621 @@ int solve_context(stokes_ctx* cp, const double* f, const double* g, double tol, 
                   stokes_info* info) {
   stokes_ctx& c = *cp;
   auto t0 = std::chrono::steady_clock::now();
+  c.sc.top = 0;
   const size_t nv = nvel(c), np = npres(c);
   Tmp<double> F(c.pool, nv);
   assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, f, F, c.tet_vol);
   int status = solve_reduced(c, F, g, tol, c.U_last, c.P_last, info, t0);
   expand_velocity(c.ex, c.n, c.U_last, u);
   copy<double>(c, p, (const double*)c.P_last, np);
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  host_sync(c);
   c.have_solution = true;
   if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return status;
+}
+
+// ===========================================================================
+// K right-hand sides in lockstep (stokes_solve_multi). The vectors below are
+// K-vectors: the velocity blocks [K][nv] followed by the pressure blocks
+// [K][np], or K plain blocks of one length. The V-cycles and Chebyshev mass
+// inverses sweep each level matrix once for all K systems (3K or K
+// component-major components), the K-RHS vector kernels serve all systems in
+// one launch, and the A, B and B^T products run once per system. Every
+// system keeps its own Krylov coefficients, Hessenberg matrix and
+// convergence test; a converged system's vectors are zeroed and ride along.
+// ===========================================================================
+constexpr int kLockstep = 4;  // right-hand sides per lockstep group (3K and K components: 12 and 4)
+
+static void read_k(stokes_ctx& c, const double* d, int slot, int count) {
+  SK_CUDA(cudaMemcpyAsync(c.sc.h + slot, d, sizeof(double) * count, cudaMemcpyDeviceToHost, c.ex.s));
+  host_sync(c);
+}
+static void read_k_issue(stokes_ctx& c, const double* d, int slot, int count) {
+  SK_CUDA(cudaMemcpyAsync(c.sc.h + slot, d, sizeof(double) * count, cudaMemcpyDeviceToHost, c.ex.s));
+  SK_CUDA(cudaEventRecord(c.ev_read, c.ex.s));
+}
+static unsigned all_bits(int K) { return K >= 32 ? ~0u : ((1u << K) - 1u); }
+static bool has_bit(unsigned m, int k) { return (m >> k) & 1u; }
+
+// r_k <- r_k - mean(r_k) for K plain blocks of length n
+template <class T> static void project_mean_k(stokes_ctx& c, T* r, size_t n, int K) {
+  const int s = c.sc.take(K);
+  kdot<T>(c.ex, c.ds, n, 0, K, 1, r, (const T*)nullptr, c.sc.d + s);
+  kaddconst<T>(c.ex, n, 0, K, 1, KCoefs::ratio(c.sc.d + s, nullptr, -1.0 / (double)n), r);
+  c.sc.give(K);
+}
+
+// per-system B and B^T products: y_k = b_k + alpha B x_k; y_k = b_k + alpha s o (B^T x_k)
+template <class T> static void b_apply_k(stokes_ctx& c, int K, const T* x, T* y, const T* b, double alpha) {
+  const size_t nv = nvel(c), np = npres(c);
+  for (int k = 0; k < K; ++k) b_apply<T>(c.ex, c.B, x + k * nv, y + k * np, b ? b + k * np : nullptr, alpha);
+}
+template <class T>
+static void bt_apply_k(stokes_ctx& c, int K, const T* x, T* y, const T* scale, const T* b, double alpha) {
+  const size_t nv = nvel(c), np = npres(c);
+  for (int k = 0; k < K; ++k)
+    bt_apply<T>(c.ex, c.Bt, x + k * np, y + k * nv, scale, b ? b + k * nv : nullptr, alpha);
+}
+
+// y_k = A_gamma x_k for K velocity blocks
+template <class T> static void op_A_k(stokes_ctx& c, int K, const T* x, T* y) {
+  const size_t nv = nvel(c), np = npres(c);
+  for (int k = 0; k < K; ++k) bsr3_apply<T>(c.ex, c.A, x + k * nv, y + k * nv, (const T*)nullptr);
+  if (c.gamma > 0.0) {
+    Tmp<T> bx(c.pool, K * np), mb(c.pool, K * np);
+    b_apply_k<T>(c, K, x, bx, (const T*)nullptr, 1.0);
+    mass_inverse<T>(c, bx, mb, c.opt.mass_steps_al, K);
+    bt_apply_k<T>(c, K, mb, y, (const T*)nullptr, y, c.gamma * c.mu);
+  }
+}
+
+// Preconditioned CG on K systems of length n in lockstep (the same
+// iteration as pcg() per system). fixed > 0: exactly `fixed` iterations, no
+// host synchronisation. Otherwise a system stops updating (its coefficients
+// masked to zero) once its residual meets rtol; the loop ends when all have.
+// op(d, q, dq) computes q_k = M d_k and dq[k] = d_k . q_k.
+template <class T, class Op, class Pre>
+static int kpcg(stokes_ctx& c, size_t n, int K, Op&& op, Pre&& pre, const T* b, T* x, double rtol, int maxit,
+                int fixed, unsigned* unconverged = nullptr) {
+  Scalars& S = c.sc;
+  const int s = S.take(5 * K);
+  double* D = S.d + s;  // [0,K), [K,2K): r.z (alternating); [2K,3K): d.q; [3K,4K): r.r; [4K,5K): b.b
+  const size_t len = (size_t)K * n;
+  Tmp<T> r(c.pool, len), z(c.pool, len), d(c.pool, len), q(c.pool, len);
+  zero<T>(c, x, len);
+  copy<T>(c, r, b, len);
+  unsigned act = all_bits(K);
+  double bn[kMaxRhs] = {};
+  if (fixed <= 0) {
+    kdot<T>(c.ex, c.ds, n, 0, K, 1, r, r, D + 4 * K);
+    read_k(c, D + 4 * K, s + 4 * K, K);
+    for (int k = 0; k < K; ++k) {
+      const double bb = S.h[s + 4 * K + k];
+      if (!std::isfinite(bb)) {
+        S.give(5 * K);
+        throw Error(STOKES_ERR_NAN, "non-finite right-hand side in an inner solve");
+      }
+      if (bb == 0.0) act &= ~(1u << k);
+      bn[k] = std::sqrt(bb);
+    }
+    if (!act) {
+      S.give(5 * K);
+      if (unconverged) *unconverged = 0;
+      return 0;
+    }
+  }
+  pre((const T*)r, (T*)z);
+  copy<T>(c, d, z, len);
+  int irz = 0, irzn = 1;
+  kdot<T>(c.ex, c.ds, n, 0, K, 1, r, z, D + irz * K);
+  int it = 0;
+  const int cap = fixed > 0 ? fixed : maxit;
+  try {
+    while (it < cap) {
+      op((const T*)d, (T*)q, D + 2 * K);
+      ++it;
+      KCoefs alpha = KCoefs::ratio(D + irz * K, D + 2 * K).mask(act);
+      KCoefs malpha = KCoefs::ratio(D + irz * K, D + 2 * K, -1.0).mask(act);
+      kaxpby<T>(c.ex, n, 0, K, 1, alpha, d, KCoefs::constant(1.0), x);
+      kaxpby<T>(c.ex, n, 0, K, 1, malpha, q, KCoefs::constant(1.0), r);
+      if (fixed > 0) {
+        if (it == cap) break;
+        pre((const T*)r, (T*)z);
+      } else {
+        kdot<T>(c.ex, c.ds, n, 0, K, 1, r, r, D + 3 * K);
+        read_k_issue(c, D + 3 * K, s + 3 * K, K);
+        pre((const T*)r, (T*)z);
+        SK_CUDA(cudaEventSynchronize(c.ev_read));
+        for (int k = 0; k < K; ++k) {
+          if (!has_bit(act, k)) continue;
+          const double rr = S.h[s + 3 * K + k];
+          if (!std::isfinite(rr)) throw Error(STOKES_ERR_NAN, "non-finite residual in an inner solve");
+          if (std::sqrt(rr) <= rtol * bn[k]) act &= ~(1u << k);
+        }
+        if (!act) break;
+      }
+      kdot<T>(c.ex, c.ds, n, 0, K, 1, r, z, D + irzn * K);
+      kaxpby<T>(c.ex, n, 0, K, 1, KCoefs::constant(1.0), z, KCoefs::cg_ratio(D + irzn * K, D + irz * K).mask(act),
+                d);
+      std::swap(irz, irzn);
+    }
+  } catch (...) {
+    S.give(5 * K);
+    throw;
+  }
+  if (unconverged) *unconverged = fixed > 0 ? 0u : act;
+  S.give(5 * K);
+  return it;
+}
+
+// A^{-1} t for K velocity blocks by PCG with V-cycles (as ainv())
+template <class T> static int ainv_k(stokes_ctx& c, int K, const T* t, T* w, double tol) {
+  const size_t nv = nvel(c);
+  unsigned left = 0;
+  int it = kpcg<T>(
+      c, nv, K,
+      [&](const T* x, T* y, double* dq) {
+        if (c.gamma > 0.0) {
+          op_A_k<T>(c, K, x, y);
+          kdot<T>(c.ex, c.ds, nv, 0, K, 1, x, (const T*)y, dq);
+        } else {
+          for (int k = 0; k < K; ++k) bsr3_apply_dot<T>(c.ex, c.A, x + k * nv, y + k * nv, c.ds, dq + k);
+        }
+      },
+      [&](const T* r, T* z) { vcycles<T>(c, velocity_cycle(c), r, z, std::max(1, c.opt.vcycles), K); }, t, w, tol,
+      c.opt.max_inner, 0, &left);
+  c.inner_iters += it;
+  if (left) c.inner_capped = true;
+  return it;
+}
+
+// Cahouet-Chabard C for K pressure blocks (as cprec_body())
+template <class T> static int cprec_body_k(stokes_ctx& c, int K, const T* r, T* z) {
+  const size_t np = npres(c), nv = nvel(c), len = (size_t)K * np;
+  Tmp<T> rp(c.pool, len), z1(c.pool, len), z2(c.pool, len);
+  copy<T>(c, rp, r, len);
+  project_mean_k<T>(c, rp, np, K);
+  mass_inverse<T>(c, rp, z1, c.opt.mass_steps, K);
+  const bool lumped = c.opt.schur_prec == STOKES_SCHUR_PREC_LUMPED;
+  const bool vmass = c.opt.schur_prec == STOKES_SCHUR_PREC_MASS;
+  const T* linv = pick<T>(c.lumped_inv64, c.lumped_inv32);
+  int it = kpcg<T>(
+      c, np, K,
+      [&](const T* p, T* y, double* dq) {
+        if (lumped) {
+          Tmp<T> t(c.pool, nv);
+          for (int k = 0; k < K; ++k) {
+            bt_apply<T>(c.ex, c.Bt, p + k * np, t, linv, (const T*)nullptr, 1.0);
+            b_apply<T>(c.ex, c.B, t, y + k * np, (const T*)nullptr, 1.0);
+          }
+        } else if (vmass) {
+          Tmp<T> t(c.pool, nv), w(c.pool, nv);
+          for (int k = 0; k < K; ++k) {
+            bt_apply<T>(c.ex, c.Bt, p + k * np, t, (const T*)nullptr, (const T*)nullptr, 1.0);
+            cheb_run<T>(c, c.MV, 3, pick<T>(c.MV_dinv64, c.MV_dinv32), kMassVLow, kMassVHigh, c.opt.mass_steps_v, t,
+                        w, true, STOKES_KERNEL_SPMM_A3);
+            b_apply<T>(c.ex, c.B, w, y + k * np, (const T*)nullptr, 1.0);
+          }
+        } else {
+          spmv_store<T>(c.ex, c.LQ, K, p, y, STOKES_KERNEL_SPMV_P1);
+        }
+        project_mean_k<T>(c, y, np, K);
+        kdot<T>(c.ex, c.ds, np, 0, K, 1, p, (const T*)y, dq);
+      },
+      [&](const T* v, T* w) {
+        Tmp<T> vp(c.pool, len);
+        copy<T>(c, vp, v, len);
+        project_mean_k<T>(c, vp, np, K);
+        vcycles<T>(c, 1, vp, w, 1, K);
+      },
+      (const T*)rp, (T*)z2, c.opt.schur_inner_tol, c.opt.max_inner, c.opt.schur_inner_iters);
+  lincomb2<T>(c.ex, len, c.mu * (1.0 + c.gamma), z1, 1.0 / c.dt, z2, z);
+  return it;
+}
+
+template <class T> static void cprec_k(stokes_ctx& c, int K, const T* r, T* z) {
+  if (!cprec_graph_ok(c)) {
+    c.schur_inner_iters += cprec_body_k<T>(c, K, r, z);
+    return;
+  }
+  c.schur_inner_iters += c.opt.schur_inner_iters;
+  graph_region(c, GraphKey(16 + (int)std::is_same<T, float>::value, 100 + K, (const void*)r, (void*)z, c.sc.top),
+               [&]() { (void)cprec_body_k<T>(c, K, r, z); });
+}
+
+template <class T> static void atilde_inv_k(stokes_ctx& c, int K, const T* r, T* z, double tol_in) {
+  if (c.opt.m2_inner_cg)
+    ainv_k<T>(c, K, r, z, tol_in);
+  else
+    vcycles<T>(c, velocity_cycle(c), r, z, std::max(1, c.opt.vcycles), K);
+}
+
+// the block preconditioner of method2 for K-vectors v -> z
+template <class T> static void block_prec_k(stokes_ctx& c, int K, const T* v, T* z, double tol_in) {
+  const size_t nv = nvel(c), np = npres(c), Kv = (size_t)K * nv;
+  Tmp<T> w(c.pool, Kv), s(c.pool, (size_t)K * np);
+  atilde_inv_k<T>(c, K, v, w, tol_in);            // w = A~^{-1} vu
+  b_apply_k<T>(c, K, w, s, v + Kv, -1.0);         // s = vp - B w
+  cprec_k<T>(c, K, s, z + Kv);                    // zp = C s
+  if (c.opt.block_lu) {
+    Tmp<T> t(c.pool, Kv), u(c.pool, Kv);
+    bt_apply_k<T>(c, K, z + Kv, t, (const T*)nullptr, (const T*)nullptr, 1.0);
+    atilde_inv_k<T>(c, K, t, u, tol_in);          // u = A~^{-1} B^T zp
+    lincomb2<T>(c.ex, Kv, 1.0, w, 1.0, u, z);     // zu = w + u
+  } else {
+    copy<T>(c, z, (const T*)w, Kv);
+  }
+}
+
+// Method 2 (right-preconditioned FGMRES(m), CGS2) for the K systems of the
+// residual K-vector R (rF blocks, then rg blocks) into the K-vector X, in
+// lockstep: one Arnoldi step of every live system per iteration, one host
+// read per iteration for all of them. eta[k]: relative reduction wanted of
+// system k; `live`: the systems to solve (others get X_k = 0); its[k] counts
+// the iterations system k took part in.
+template <class T>
+static void method2_k(stokes_ctx& c, int K, const T* R, T* X, const double* eta, double tol_in, unsigned live,
+                      int* its) {
+  const size_t nv = nvel(c), np = npres(c), Kv = (size_t)K * nv, KN = (size_t)K * (nv + np);
+  const int m = std::max(2, c.opt.restart);
+  const int ld = m + 1;
+  std::vector<std::unique_ptr<Tmp<T>>> V, Z;
+  for (int j = 0; j <= m; ++j) V.emplace_back(new Tmp<T>(c.pool, KN));
+  for (int j = 0; j < m; ++j) Z.emplace_back(new Tmp<T>(c.pool, KN));
+  Scalars& S = c.sc;
+  const int nsl = K * (2 * ld + 2);
+  const int s = S.take(nsl);
+  struct Give {
+    Scalars& S;
+    int n;
+    ~Give() { S.give(n); }
+  } give{S, nsl};
+  double* D = S.d + s;                 // [0,K): norms
+  double* h0 = D + K;                  // [K][ld]: first Gram-Schmidt pass
+  double* h1 = D + K + K * ld;         // [K][ld]: second pass
+  double* ww = D + K + 2 * K * ld;     // [K]: w . w
+  const double* H0 = S.h + s + K;
+  const double* H1 = S.h + s + K + K * ld;
+  const double* WW = S.h + s + K + 2 * K * ld;
+  Tmp<T> Fg(c.pool, c.gamma > 0.0 ? Kv : 1);
+  const T* F = R;
+  const T* rg = R + Kv;
+  if (c.gamma > 0.0) {
+    Tmp<T> mg(c.pool, (size_t)K * np);
+    mass_inverse<T>(c, rg, mg, c.opt.mass_steps_al, K);
+    bt_apply_k<T>(c, K, mg, Fg, (const T*)nullptr, R, c.gamma * c.mu);
+    F = Fg;
+  }
+  zero<T>(c, X, KN);
+  T* v0 = *V[0];
+  copy<T>(c, v0, F, Kv);
+  copy<T>(c, v0 + Kv, rg, (size_t)K * np);
+  project_mean_k<T>(c, v0 + Kv, np, K);
+  kdot<T>(c.ex, c.ds, nv, np, K, 3, v0, v0, D);
+  read_k(c, D, s, K);
+  double beta0[kMaxRhs] = {}, beta[kMaxRhs] = {};
+  for (int k = 0; k < K; ++k) {
+    beta0[k] = beta[k] = std::sqrt(S.h[s + k]);
+    if (!std::isfinite(beta0[k])) throw Error(STOKES_ERR_NAN, "non-finite coupled right-hand side");
+    if (beta0[k] == 0.0) live &= ~(1u << k);
+  }
+  int total = 0;
+  std::vector<double> H((size_t)K * ld * m), cs((size_t)K * m), sn((size_t)K * m), g((size_t)K * ld), y(m);
+  std::vector<double> coef((size_t)K * kMaxBasisK);
+  int jk[kMaxRhs] = {};
+  while (live && total < c.opt.max_outer) {
+    double scl[kMaxRhs] = {};
+    for (int k = 0; k < K; ++k) scl[k] = has_bit(live, k) ? 1.0 / beta[k] : 0.0;
+    kaxpby<T>(c.ex, nv, np, K, 3, KCoefs::host(scl, K), *V[0], KCoefs::constant(0.0), *V[0]);
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int k = 0; k < K; ++k) g[(size_t)k * ld] = beta[k], jk[k] = 0;
+    unsigned act = live, conv = 0;
+    int j = 0;
+    for (; j < m && total < c.opt.max_outer; ++j, ++total) {
+      T* vj = *V[j];
+      T* zj = *Z[j];
+      T* w = *V[j + 1];
+      block_prec_k<T>(c, K, vj, zj, tol_in);
+      op_A_k<T>(c, K, zj, w);                                           // w = K zj
+      bt_apply_k<T>(c, K, zj + Kv, w, (const T*)nullptr, w, -1.0);
+      b_apply_k<T>(c, K, zj, w + Kv, (const T*)nullptr, 1.0);
+      for (int pass = 0; pass < 2; ++pass) {                           // CGS2
+        double* h = pass ? h1 : h0;
+        const T* vs[kMaxBasisK];
+        for (int i = 0; i <= j; i += kMaxBasisK) {
+          const int kk = std::min(kMaxBasisK, j + 1 - i);
+          for (int t = 0; t < kk; ++t) vs[t] = *V[i + t];
+          kmdot<T>(c.ex, c.ds, nv, np, K, kk, vs, w, h + i, ld);
+        }
+        for (int i = 0; i <= j; i += kMaxBasisK) {
+          const int kk = std::min(kMaxBasisK, j + 1 - i);
+          for (int t = 0; t < kk; ++t) vs[t] = *V[i + t];
+          kmaxpy<T>(c.ex, nv, np, K, kk, vs, h + i, nullptr, ld, -1.0, w);
+        }
+      }
+      kdot<T>(c.ex, c.ds, nv, np, K, 3, w, w, ww);
+      read_k(c, D, s, nsl);
+      double wscale[kMaxRhs] = {};
+      for (int k = 0; k < K; ++k) {
+        if (!has_bit(act, k)) continue;
+        ++its[k];
+        double* Hk = H.data() + (size_t)k * ld * m;
+        double* ck = cs.data() + (size_t)k * m;
+        double* sk_ = sn.data() + (size_t)k * m;
+        double* gk = g.data() + (size_t)k * ld;
+        const double hn = std::sqrt(WW[k]);
+        if (!std::isfinite(hn)) throw Error(STOKES_ERR_NAN, "non-finite Arnoldi vector");
+        for (int i = 0; i <= j; ++i) Hk[i * m + j] = H0[k * ld + i] + H1[k * ld + i];
+        Hk[(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {  // Givens
+          const double a = Hk[i * m + j], b = Hk[(i + 1) * m + j];
+          Hk[i * m + j] = ck[i] * a + sk_[i] * b;
+          Hk[(i + 1) * m + j] = -sk_[i] * a + ck[i] * b;
+        }
+        const double a = Hk[j * m + j], b = Hk[(j + 1) * m + j];
+        const double rden = std::hypot(a, b);
+        ck[j] = rden > 0 ? a / rden : 1.0;
+        sk_[j] = rden > 0 ? b / rden : 0.0;
+        Hk[j * m + j] = rden;
+        Hk[(j + 1) * m + j] = 0.0;
+        gk[j + 1] = -sk_[j] * gk[j];
+        gk[j] = ck[j] * gk[j];
+        jk[k] = j + 1;
+        if (std::fabs(gk[j + 1]) <= eta[k] * beta0[k] || hn == 0.0) {
+          act &= ~(1u << k);
+          conv |= 1u << k;
+        } else {
+          wscale[k] = 1.0 / hn;
+        }
+      }
+      // next basis vector: w_k / |w_k| for systems still iterating, 0 for the rest
+      kaxpby<T>(c.ex, nv, np, K, 3, KCoefs::host(wscale, K), w, KCoefs::constant(0.0), w);
+      if (!act) {
+        ++j;
+        ++total;
+        break;
+      }
+    }
+    // X_k += Z y_k, y_k = H_k^{-1} g_k over the jk[k] columns system k built
+    int jmax = 0;
+    for (int k = 0; k < K; ++k)
+      if (has_bit(live, k)) jmax = std::max(jmax, jk[k]);
+    std::vector<double> Y((size_t)K * m, 0.0);
+    for (int k = 0; k < K; ++k) {
+      if (!has_bit(live, k)) continue;
+      const double* Hk = H.data() + (size_t)k * ld * m;
+      const double* gk = g.data() + (size_t)k * ld;
+      double* yk = Y.data() + (size_t)k * m;
+      for (int i = jk[k] - 1; i >= 0; --i) {
+        double t = gk[i];
+        for (int q = i + 1; q < jk[k]; ++q) t -= Hk[i * m + q] * yk[q];
+        yk[i] = t / Hk[i * m + i];
+      }
+    }
+    for (int i = 0; i < jmax; i += kMaxBasisK) {
+      const int kk = std::min(kMaxBasisK, jmax - i);
+      const T* zs[kMaxBasisK];
+      for (int t = 0; t < kk; ++t) zs[t] = *Z[i + t];
+      for (int k = 0; k < K; ++k)
+        for (int t = 0; t < kk; ++t) coef[(size_t)k * kk + t] = Y[(size_t)k * m + i + t];
+      kmaxpy<T>(c.ex, nv, np, K, kk, zs, nullptr, coef.data(), kk, 1.0, X);
+    }
+    live &= ~conv;
+    if (!live || total >= c.opt.max_outer) break;
+    // restart: r = [F; rg] - K X
+    T* r0 = *V[0];
+    op_A_k<T>(c, K, X, r0);
+    bt_apply_k<T>(c, K, X + Kv, r0, (const T*)nullptr, r0, -1.0);
+    axpby<T>(c.ex, Kv, Coef::constant(1.0), F, Coef::constant(-1.0), r0);
+    b_apply_k<T>(c, K, X, r0 + Kv, rg, -1.0);
+    project_mean_k<T>(c, r0 + Kv, np, K);
+    kdot<T>(c.ex, c.ds, nv, np, K, 3, r0, r0, D);
+    read_k(c, D, s, K);
+    for (int k = 0; k < K; ++k) {
+      if (!has_bit(live, k)) continue;
+      beta[k] = std::sqrt(S.h[s + k]);
+      if (!std::isfinite(beta[k])) throw Error(STOKES_ERR_NAN, "non-finite coupled residual");
+      if (beta[k] <= eta[k] * beta0[k]) live &= ~(1u << k);
+    }
+  }
+  c.outer_iters += total;
+  if (live) c.outer_capped = true;
+}
+
+// full FP64 residuals of K systems: R = [F - A U + B^T P; g - B U] (K-vectors
+// of the solutions X), rel[k] = |R_k| / normFg[k]
+static void full_residual_k(stokes_ctx& c, int K, const double* F, const double* g, const double* X, double* R,
+                            const double* normFg, double* rel) {
+  const size_t nv = nvel(c), np = npres(c), Kv = (size_t)K * nv;
+  for (int k = 0; k < K; ++k) {
+    const double* Uk = X + k * nv;
+    double* rFk = R + k * nv;
+    if (c.A.v32lo) {
+      Tmp<float> uh(c.pool, nv), ul(c.pool, nv);
+      split_f64(c.ex, nv, Uk, uh, ul);
+      bsr3_residual_df(c.ex, c.A, uh, ul, F + k * nv, rFk, STOKES_KERNEL_RESIDUAL);
+    } else {
+      bsr3_apply<double>(c.ex, c.A, Uk, rFk, F + k * nv, STOKES_KERNEL_RESIDUAL);
+    }
+    bt_apply<double>(c.ex, c.Bt, X + Kv + k * np, rFk, (const double*)nullptr, rFk, 1.0);
+    b_apply<double>(c.ex, c.B, Uk, R + Kv + k * np, g + k * np, -1.0);
+  }
+  const int s = c.sc.take(K);
+  kdot<double>(c.ex, c.ds, nv, np, K, 3, R, R, c.sc.d + s);
+  read_k(c, c.sc.d + s, s, K);
+  for (int k = 0; k < K; ++k) rel[k] = normFg[k] > 0 ? std::sqrt(c.sc.h[s + k]) / normFg[k] : 0.0;
+  c.sc.give(K);
+}
+
+template <class T>
+static void correction_k(stokes_ctx& c, int K, const double* R, double* X, const double* eta, double tol_in,
+                         unsigned live, int* its) {
+  const size_t KN = (size_t)K * (nvel(c) + npres(c));
+  Tmp<T> dX(c.pool, KN);
+  Tmp<T> R32(c.pool, std::is_same<T, double>::value ? 1 : KN);
+  const T* Rt;
+  if constexpr (std::is_same<T, double>::value) {
+    Rt = R;
+  } else {
+    convert<double, float>(c.ex, KN, R, R32);
+    Rt = R32;
+  }
+  method2_k<T>(c, K, Rt, dX, eta, tol_in, live, its);
+  add_convert<T, double>(c.ex, KN, dX, X);
+}
+
+// K systems K [U_k; P_k] = [F_k; g_k] in the reduced spaces (as
+// solve_reduced()): F [K][nv], g [K][np] or null, solutions into the
+// K-vector X; info[k] and the returned status per system in status[k].
+static void solve_reduced_k(stokes_ctx& c, int K, const double* F, const double* g, double tol, double* X,
+                            stokes_info* info, int* status, std::chrono::steady_clock::time_point t0) {
+  const size_t nv = nvel(c), np = npres(c), Kv = (size_t)K * nv, KN = (size_t)K * (nv + np);
+  c.outer_iters = c.inner_iters = c.schur_inner_iters = 0;
+  c.outer_capped = c.inner_capped = false;
+  SK_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.ex.s));
+  Tmp<double> gz(c.pool, (size_t)K * np), R(c.pool, KN);
+  const double* gp = g;
+  if (!gp) {
+    zero<double>(c, gz, (size_t)K * np);
+    gp = gz;
+  }
+  double normFg[kMaxRhs] = {}, rel[kMaxRhs] = {};
+  {
+    const int s = c.sc.take(3 * K);
+    kdot<double>(c.ex, c.ds, np, 0, K, 1, gp, (const double*)nullptr, c.sc.d + s);
+    kdot<double>(c.ex, c.ds, np, 0, K, 1, gp, gp, c.sc.d + s + K);
+    kdot<double>(c.ex, c.ds, nv, 0, K, 1, F, F, c.sc.d + s + 2 * K);
+    read_k(c, c.sc.d + s, s, 3 * K);
+    for (int k = 0; k < K; ++k) {
+      const double gsum = c.sc.h[s + k], gg = c.sc.h[s + K + k], FF = c.sc.h[s + 2 * K + k];
+      if (!std::isfinite(gsum) || !std::isfinite(gg) || !std::isfinite(FF)) {
+        c.sc.give(3 * K);
+        throw Error(STOKES_ERR_NAN, "non-finite right-hand side");
+      }
+      if (std::fabs(gsum) > 1e-10 * std::sqrt((double)np * gg) + 1e-300) {
+        c.sc.give(3 * K);
+        throw Error(STOKES_ERR_INCOMPATIBLE_RHS, "sum(g) must vanish for B u = g to be solvable");
+      }
+      normFg[k] = std::sqrt(FF + gg);
+    }
+    c.sc.give(3 * K);
+  }
+  zero<double>(c, X, KN);
+  unsigned pending = 0;
+  int refinements[kMaxRhs] = {}, its[kMaxRhs] = {};
+  for (int k = 0; k < K; ++k) {
+    status[k] = STOKES_OK;
+    if (normFg[k] > 0) pending |= 1u << k;
+  }
+  try {
+    for (int pass = 0; pending; ++pass) {
+      full_residual_k(c, K, F, gp, X, R, normFg, rel);
+      double eta[kMaxRhs] = {};
+      const bool passes = c.opt.pass_schedule == 1 || (c.opt.pass_schedule == 0 && c.mixed);
+      for (int k = 0; k < K; ++k) {
+        if (!has_bit(pending, k)) continue;
+        refinements[k] = pass;
+        if (!std::isfinite(rel[k])) {
+          status[k] = STOKES_ERR_NAN;
+          pending &= ~(1u << k);
+        } else if (rel[k] <= tol) {
+          pending &= ~(1u << k);
+        } else if (pass >= c.opt.max_refine) {
+          status[k] = STOKES_ERR_NOT_CONVERGED;
+          pending &= ~(1u << k);
+        }
+        eta[k] = passes ? std::max(c.opt.pass_tol, 0.5 * tol / rel[k]) : std::max(0.5 * tol / rel[k], 1e-13);
+      }
+      if (!pending) break;
+      const double tin = passes ? std::max(c.opt.inner_tol, c.opt.pass_tol / 30.0) : c.opt.inner_tol;
+      if (c.mixed)
+        correction_k<float>(c, K, R, X, eta, tin, pending, its);
+      else
+        correction_k<double>(c, K, R, X, eta, tin, pending, its);
+    }
+  } catch (const Error& e) {
+    if (e.status == STOKES_ERR_NAN && (read_flag(c) & 1))
+      throw Error(STOKES_ERR_BREAKDOWN, std::string("Krylov breakdown (r^T z <= 0 or p^T A p <= 0), then ") + e.what());
+    throw;
+  }
+  // int p_h = 0 per system
+  {
+    const int s2 = c.sc.take(1);
+    for (int k = 0; k < K; ++k) {
+      double* Pk = X + Kv + k * np;
+      dot1<double>(c, (const double*)c.MQ1, (const double*)Pk, np, c.sc.d + s2);
+      sub_mean<double>(c.ex, np, c.sc.d + s2, c.MQ1_sum, Pk);
+    }
+    c.sc.give(1);
+  }
+  const int flag = read_flag(c);
+  for (int k = 0; k < K; ++k) {
+    if ((status[k] == STOKES_ERR_NOT_CONVERGED || status[k] == STOKES_ERR_NAN) && (flag & 1))
+      status[k] = STOKES_ERR_BREAKDOWN;
+    if (flag & 4) status[k] = STOKES_ERR_TIMEOUT;
+    if (info) {
+      info[k].outer_iters = its[k];
+      info[k].inner_iters = c.inner_iters;
+      info[k].refinements = refinements[k];
+      info[k].status = status[k];
+      info[k].rel_residual = rel[k];
+      info[k].solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+}
+
+// K forces f [K][(2n+1)^3][3] -> u [K][(2n+1)^3][3], p [K][(n+1)^3]. Method 2
+// solves groups of kLockstep systems in lockstep (a short last group is padded
+// with zero systems; a single one takes the one-system path); Method 1 solves
+// the systems one after another.
+int solve_multi_context(stokes_ctx* cp, int K, const double* f, const double* g, double tol, double* u, double* p,
+                        stokes_info* info) {
+  stokes_ctx& c = *cp;
+  auto t0 = std::chrono::steady_clock::now();
+  c.sc.top = 0;
+  const size_t nv = nvel(c), np = npres(c);
+  const size_t Nall = 3 * (size_t)(2 * c.n + 1) * (2 * c.n + 1) * (2 * c.n + 1);
+  int worst = STOKES_OK;
+  auto note = [&](int st) {
+    if (worst == STOKES_OK && st != STOKES_OK) worst = st;
+  };
+  for (int k0 = 0; k0 < K;) {
+    const int left = K - k0;
+    if (c.opt.method != STOKES_METHOD_COUPLED || left == 1) {
+      note(solve_context(cp, f + k0 * Nall, g ? g + k0 * np : nullptr, tol, u + k0 * Nall, p + k0 * np,
+                         info ? info + k0 : nullptr));
+      ++k0;
+      continue;
+    }
+    const int kb = std::min(kLockstep, left), W = kLockstep;
+    Tmp<double> F(c.pool, (size_t)W * nv), X(c.pool, (size_t)W * (nv + np));
+    Tmp<double> G(c.pool, g ? (size_t)W * np : 1);
+    for (int k = 0; k < kb; ++k) assemble_load(c.ex, c.n, c.lv[0].X, c.lv[0].A3, f + (k0 + k) * Nall, F + k * nv, c.tet_vol);
+    if (kb < W) zero<double>(c, F + kb * nv, (size_t)(W - kb) * nv);
+    if (g) {
+      copy<double>(c, G, g + k0 * np, (size_t)kb * np);
+      if (kb < W) zero<double>(c, G + kb * np, (size_t)(W - kb) * np);
+    }
+    stokes_info inf[kLockstep] = {};
+    int st[kLockstep] = {};
+    solve_reduced_k(c, W, F, g ? (const double*)G : nullptr, tol, X, inf, st, t0);
+    for (int k = 0; k < kb; ++k) {
+      expand_velocity(c.ex, c.n, X + k * nv, u + (k0 + k) * Nall);
+      copy<double>(c, p + (k0 + k) * np, (const double*)(X + (size_t)W * nv + k * np), np);
+      if (info) info[k0 + k] = inf[k];
+      note(st[k]);
+    }
+    // the last system's solution serves a following stokes_adjoint
+    copy<double>(c, c.U_last, (const double*)(X + (kb - 1) * nv), nv);
+    copy<double>(c, c.P_last, (const double*)(X + (size_t)W * nv + (kb - 1) * np), np);
+    c.have_solution = true;
+    k0 += kb;
+  }
+  host_sync(c);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info)
+    for (int k = 0; k < K; ++k) info[k].solve_ms = ms;
+  return worst;
 }
 
 // Adjoint. K = [A -B^T; B 0] has K^T = [A B^T; -B 0]; with lp = -P' the
@@ -1105,7 +1728,7 @@ int adjoint_context(stokes_ctx* cp, const double* dJdu, const double* dJdp, doub
     *dJdmu = -read_now(c, c.sc.d + s, s);
     c.sc.give(1);
   }
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  host_sync(c);
   if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return status;
 }
@@ -1183,7 +1806,7 @@ void apply_operator(stokes_ctx* cp, int op, int level, const double* x, double* 
     default: throw Error(STOKES_ERR_ARG, "unknown operator");
   }
   (void)np;
-  SK_CUDA(cudaStreamSynchronize(c.ex.s));
+  host_sync(c);
 }
 
 // ---------------------------------------------------------------------------

@@ -85,6 +85,7 @@ ProfScope::~ProfScope() {
 // Vectors with NR components are component-major: component r of row i at
 // r * ns + i (ns = number of rows of the vector).
 template <class T, int NR> struct EpiStore {
+  static constexpr int nr = NR;
   T* y;
   size_t ns;
   __device__ __forceinline__ void operator()(int row, const T* acc) const {
@@ -93,6 +94,7 @@ template <class T, int NR> struct EpiStore {
   }
 };
 template <class T, int NR> struct EpiAdd {
+  static constexpr int nr = NR;
   T* y;
   size_t ns;
   __device__ __forceinline__ void operator()(int row, const T* acc) const {
@@ -100,7 +102,8 @@ template <class T, int NR> struct EpiAdd {
     for (int r = 0; r < NR; ++r) y[r * ns + row] += acc[r];
   }
 };
-template <class T, int NR> struct EpiResid {  // y = b - acc
+template <class T, int NR> struct EpiResid {
+  static constexpr int nr = NR;  // y = b - acc
   const T* b;
   T* y;
   size_t ns;
@@ -109,7 +112,8 @@ template <class T, int NR> struct EpiResid {  // y = b - acc
     for (int r = 0; r < NR; ++r) y[r * ns + row] = b[r * ns + row] - acc[r];
   }
 };
-template <class T, int NR> struct EpiAxpy {  // y = (b ? b : 0) + alpha * s_row * acc
+template <class T, int NR> struct EpiAxpy {
+  static constexpr int nr = NR;  // y = (b ? b : 0) + alpha * s_row * acc
   const T* b;
   const T* s;
   T* y;
@@ -128,6 +132,7 @@ template <class T, int NR> struct EpiAxpy {  // y = (b ? b : 0) + alpha * s_row 
 // Chebyshev semi-iteration step (Saad, Iterative Methods, Alg. 12.1):
 // r = b - A x_in; d = c1 d + c2 D^{-1} r; x_out = x_in + d.
 template <class T, int NR> struct EpiCheb {
+  static constexpr int nr = NR;
   const T* b;
   const T* xin;
   T* d;
@@ -150,6 +155,7 @@ template <class T, int NR> struct EpiCheb {
 
 // Same step with a diagonal per component (3x3-block operators): dinv[r*ns+row]
 template <class T> struct EpiCheb3 {
+  static constexpr int nr = 3;
   const T* b;
   const T* xin;
   T* d;
@@ -583,10 +589,8 @@ static void launch_stencil(const Exec& ex, const StencilOp& so, int nr, const T*
   if (grid == 0) return;
   size_t xs = 0;
   for (int c = 0; c < so.ncls; ++c) xs += so.rows[c];
-  if (nr == 3)
-    k_stencil<3, T, T, Epi><<<grid, bs, 0, ex.s>>>(a, so.template v<T>(), x, xs, epi);
-  else
-    k_stencil<1, T, T, Epi><<<grid, bs, 0, ex.s>>>(a, so.template v<T>(), x, xs, epi);
+  (void)nr;
+  k_stencil<Epi::nr, T, T, Epi><<<grid, bs, 0, ex.s>>>(a, so.template v<T>(), x, xs, epi);
   SK_CHECK_LAUNCH();
 }
 
@@ -605,7 +609,7 @@ static double stencil_bytes(const StencilOp& so, int esz, int nr, int streams) {
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
-enum Shape { SH_CSR1 = 0, SH_CSR3 = 1, SH_BSR3 = 2, SH_B = 3, SH_BT = 4 };
+enum Shape { SH_CSR = 0, SH_BSR3 = 2, SH_B = 3, SH_BT = 4 };  // CSR: right-hand sides from the epilogue
 
 template <int G, class T, class Epi>
 static void launch_g(const Exec& ex, const Csr& m, Shape sh, const T* x, const Epi& epi) {
@@ -613,26 +617,20 @@ static void launch_g(const Exec& ex, const Csr& m, Shape sh, const T* x, const E
   int grid = cdiv((long long)m.rows * G, bs);
   if (grid == 0) return;
   switch (sh) {
-    case SH_CSR1:
-      if constexpr (std::is_same<T, float>::value)
-        k_csr<G, 1, float, float, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v32, x, m.cols, epi);
-      else
-        k_csr<G, 1, double, double, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, x, m.cols, epi);
-      break;
-    case SH_CSR3:
-      if constexpr (std::is_same<T, float>::value)
-        k_csr<G, 3, float, float, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v32, x, m.cols, epi);
-      else
-        k_csr<G, 3, double, double, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.v64, x, m.cols, epi);
+    case SH_CSR:
+      k_csr<G, Epi::nr, T, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), x, m.cols, epi);
       break;
     case SH_BSR3:
-      k_bsr3<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
+      if constexpr (Epi::nr == 3)
+        k_bsr3<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
       break;
     case SH_B:
-      k_b<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
+      if constexpr (Epi::nr == 1)
+        k_b<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
       break;
     case SH_BT:
-      k_bt<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
+      if constexpr (Epi::nr == 3)
+        k_bt<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
       break;
   }
   SK_CHECK_LAUNCH();
@@ -656,51 +654,61 @@ static double prod_bytes(const Csr& m, int esz, int nr_in, int nr_out, int extra
   return m.bytes(esz) + (double)esz * ((double)m.cols * nr_in + (double)m.rows * nr_out * (1 + extra_streams));
 }
 
-template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
-  if (use_stencil<T>(m)) {
-    ProfScope ps(ex, kind, stencil_bytes(*m.st, sizeof(T), nr, 0));
-    if (nr == 3) launch_stencil(ex, *m.st, 3, x, EpiStore<T, 3>{y, (size_t)m.rows});
-    else launch_stencil(ex, *m.st, 1, x, EpiStore<T, 1>{y, (size_t)m.rows});
-    return;
+// calls f(std::integral_constant<int, NR>) for the supported right-hand-side
+// counts: 1 and 3 (one pressure or velocity vector), 4 and 12 (four of them)
+template <class F> static void with_nr(int nr, F&& f) {
+  switch (nr) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 3: f(std::integral_constant<int, 3>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 12: f(std::integral_constant<int, 12>()); break;
+    default: throw Error(STOKES_ERR_ARG, "sparse product: unsupported number of right-hand sides");
   }
-  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 0));
-  if (nr == 3) launch(ex, m, SH_CSR3, x, EpiStore<T, 3>{y, (size_t)m.rows}, m.group);
-  else launch(ex, m, SH_CSR1, x, EpiStore<T, 1>{y, (size_t)m.rows}, m.group);
+}
+
+template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
+  const bool st = use_stencil<T>(m);
+  ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 0) : prod_bytes(m, sizeof(T), nr, nr, 0));
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    const EpiStore<T, NR> e{y, (size_t)m.rows};
+    if (st) launch_stencil(ex, *m.st, NR, x, e);
+    else launch(ex, m, SH_CSR, x, e, m.group);
+  });
 }
 template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
-  if (use_stencil<T>(m)) {
-    ProfScope ps(ex, kind, stencil_bytes(*m.st, sizeof(T), nr, 1));
-    if (nr == 3) launch_stencil(ex, *m.st, 3, x, EpiAdd<T, 3>{y, (size_t)m.rows});
-    else launch_stencil(ex, *m.st, 1, x, EpiAdd<T, 1>{y, (size_t)m.rows});
-    return;
-  }
-  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 1));
-  if (nr == 3) launch(ex, m, SH_CSR3, x, EpiAdd<T, 3>{y, (size_t)m.rows}, m.group);
-  else launch(ex, m, SH_CSR1, x, EpiAdd<T, 1>{y, (size_t)m.rows}, m.group);
+  const bool st = use_stencil<T>(m);
+  ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    const EpiAdd<T, NR> e{y, (size_t)m.rows};
+    if (st) launch_stencil(ex, *m.st, NR, x, e);
+    else launch(ex, m, SH_CSR, x, e, m.group);
+  });
 }
 template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind) {
-  if (use_stencil<T>(m)) {
-    ProfScope ps(ex, kind, stencil_bytes(*m.st, sizeof(T), nr, 1));
-    if (nr == 3) launch_stencil(ex, *m.st, 3, x, EpiResid<T, 3>{b, y, (size_t)m.rows});
-    else launch_stencil(ex, *m.st, 1, x, EpiResid<T, 1>{b, y, (size_t)m.rows});
-    return;
-  }
-  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 1));
-  if (nr == 3) launch(ex, m, SH_CSR3, x, EpiResid<T, 3>{b, y, (size_t)m.rows}, m.group);
-  else launch(ex, m, SH_CSR1, x, EpiResid<T, 1>{b, y, (size_t)m.rows}, m.group);
+  const bool st = use_stencil<T>(m);
+  ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    const EpiResid<T, NR> e{b, y, (size_t)m.rows};
+    if (st) launch_stencil(ex, *m.st, NR, x, e);
+    else launch(ex, m, SH_CSR, x, e, m.group);
+  });
 }
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin, T* d, T* xout,
                                   const T* dinv, double c1, double c2, int kind) {
-  if (use_stencil<T>(m)) {
-    ProfScope ps(ex, kind, stencil_bytes(*m.st, sizeof(T), nr, 4) + (double)sizeof(T) * m.rows);
-    if (nr == 3) launch_stencil(ex, *m.st, 3, xin, EpiCheb<T, 3>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
-    else launch_stencil(ex, *m.st, 1, xin, EpiCheb<T, 1>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
-    return;
-  }
+  const bool st = use_stencil<T>(m);
   // streams: b, x_in (own row), d read, d write, x_out write, dinv
-  ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), nr, nr, 4) + (double)sizeof(T) * m.rows);
-  if (nr == 3) launch(ex, m, SH_CSR3, xin, EpiCheb<T, 3>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
-  else launch(ex, m, SH_CSR1, xin, EpiCheb<T, 1>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, m.group);
+  ProfScope ps(ex, kind,
+               (st ? stencil_bytes(*m.st, sizeof(T), nr, 4) : prod_bytes(m, sizeof(T), nr, nr, 4)) +
+                   (double)sizeof(T) * m.rows);
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    const EpiCheb<T, NR> e{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows};
+    if (st) launch_stencil(ex, *m.st, NR, xin, e);
+    else launch(ex, m, SH_CSR, xin, e, m.group);
+  });
 }
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
                                   const T* dinv, double c1, double c2, int kind) {
@@ -783,8 +791,7 @@ __global__ void k_dense(const T* __restrict__ M, int m, const T* __restrict__ b,
 template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y) {
   ProfScope ps(ex, STOKES_KERNEL_OTHER, (double)sizeof(T) * ((double)m * m + 2.0 * m * nr));
   int grid = cdiv(m, 8);
-  if (nr == 3) k_dense<3, T><<<grid, 256, 0, ex.s>>>(Minv, m, b, y);
-  else k_dense<1, T><<<grid, 256, 0, ex.s>>>(Minv, m, b, y);
+  with_nr(nr, [&](auto NRc) { k_dense<decltype(NRc)::value, T><<<grid, 256, 0, ex.s>>>(Minv, m, b, y); });
   SK_CHECK_LAUNCH();
 }
 
@@ -837,7 +844,7 @@ static void tune_store(const std::string& key, int g) {
 
 void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   if (m.rows == 0) return;
-  Shape sh = kind == 1 ? SH_BSR3 : kind == 2 ? SH_B : kind == 3 ? SH_BT : (nr == 3 ? SH_CSR3 : SH_CSR1);
+  Shape sh = kind == 1 ? SH_BSR3 : kind == 2 ? SH_B : kind == 3 ? SH_BT : SH_CSR;
   int xin = (sh == SH_BSR3 || sh == SH_B) ? 3 : (sh == SH_BT ? 1 : nr);
   int yout = (sh == SH_BSR3 || sh == SH_BT) ? 3 : (sh == SH_B ? 1 : nr);
   bool f32 = m.v64 == nullptr;
