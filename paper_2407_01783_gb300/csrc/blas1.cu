@@ -465,6 +465,61 @@ template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* di
   SK_CHECK_LAUNCH();
 }
 
+// node-interleaved vectors: row i's nr values at i * nr (one thread per row)
+template <class T, int NR>
+__global__ void k_cheb_first_il(size_t n, const T* __restrict__ dinv, const T* __restrict__ b, T c,
+                                T* __restrict__ d, T* __restrict__ x) {
+  SK_LOOP(i) {
+    const T s = c * dinv[i];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T v = s * b[i * NR + r];
+      d[i * NR + r] = v;
+      x[i * NR + r] = v;
+    }
+  }
+}
+template <class T>
+void cheb_first_il(const Exec& ex, size_t n, int nr, const T* dinv, const T* b, double c, T* d, T* x) {
+  if (!n) return;
+  SK_REQUIRE(nr == 4 || nr == 12, STOKES_ERR_ARG, "interleaved vectors need 4 or 12 components");
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, (double)sizeof(T) * (n * 3 + n / nr));
+  const size_t rows = n / nr;
+  if (nr == 4) k_cheb_first_il<T, 4><<<SK_GRID(rows)>>>(rows, dinv, b, (T)c, d, x);
+  else k_cheb_first_il<T, 12><<<SK_GRID(rows)>>>(rows, dinv, b, (T)c, d, x);
+  SK_CHECK_LAUNCH();
+}
+
+// [nr][rows] <-> [rows][nr]: a thread per row reads its nr components (each
+// read coalesced across the warp) and writes them contiguously, or back
+template <class T, int NR, bool TO_IL>
+__global__ void k_relayout(size_t n, const T* __restrict__ src, T* __restrict__ dst) {
+  // n rows
+  SK_LOOP(i) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (TO_IL) dst[i * NR + r] = src[r * n + i];
+      else dst[r * n + i] = src[i * NR + r];
+    }
+  }
+}
+template <class T> void to_interleaved(const Exec& ex, size_t rows, int nr, const T* cm, T* il) {
+  if (!rows) return;
+  SK_REQUIRE(nr == 4 || nr == 12, STOKES_ERR_ARG, "interleaved vectors need 4 or 12 components");
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, 2.0 * sizeof(T) * rows * nr);
+  if (nr == 4) k_relayout<T, 4, true><<<SK_GRID(rows)>>>(rows, cm, il);
+  else k_relayout<T, 12, true><<<SK_GRID(rows)>>>(rows, cm, il);
+  SK_CHECK_LAUNCH();
+}
+template <class T> void to_component_major(const Exec& ex, size_t rows, int nr, const T* il, T* cm) {
+  if (!rows) return;
+  SK_REQUIRE(nr == 4 || nr == 12, STOKES_ERR_ARG, "interleaved vectors need 4 or 12 components");
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, 2.0 * sizeof(T) * rows * nr);
+  if (nr == 4) k_relayout<T, 4, false><<<SK_GRID(rows)>>>(rows, il, cm);
+  else k_relayout<T, 12, false><<<SK_GRID(rows)>>>(rows, il, cm);
+  SK_CHECK_LAUNCH();
+}
+
 template <class S, class D> __global__ void k_convert(size_t n, const S* __restrict__ x, D* __restrict__ y) {
   SK_LOOP(i) {
     y[i] = (D)x[i];
@@ -569,6 +624,9 @@ void scalar_sub(const Exec& ex, double* out, const double* a, const double* b) {
   template void sub_mean<T>(const Exec&, size_t, const double*, double, T*);                           \
   template void sub_ratio<T>(const Exec&, size_t, const double*, const double*, T*);                   \
   template void cheb_first<T>(const Exec&, size_t, int, const T*, const T*, double, T*, T*);             \
+  template void cheb_first_il<T>(const Exec&, size_t, int, const T*, const T*, double, T*, T*);          \
+  template void to_interleaved<T>(const Exec&, size_t, int, const T*, T*);                              \
+  template void to_component_major<T>(const Exec&, size_t, int, const T*, T*);                          \
   template void mdot<T>(const Exec&, const DotScratch&, int, const T* const*, const T*, size_t, double*);  \
   template void maxpy<T>(const Exec&, int, const double*, const double*, double, const T* const*, T*, size_t);
 SK_INST1(float)

@@ -435,23 +435,29 @@ void subsample_vertices(int nf, int nc, const double* Xf_host, double* Xc_host);
 // ---------------------------------------------------------------------------
 // sparse products (sparse.cu); T = vector/matrix precision
 // ---------------------------------------------------------------------------
-// y = A x for scalar CSR with NR interleaved right-hand sides.
-template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind);
+// y = A x for a scalar matrix on nr right-hand sides (nr = 1, 3, 4 or 12):
+// component-major vectors (component r of row i at r * rows + i), or with il
+// node-interleaved ones (at i * nr + r; nr = 4 or 12).
+template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind,
+                                   bool il = false);
 // y = b - A x
-template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind);
+template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind,
+                                   bool il = false);
 // y += A x
-template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind);
+template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il = false);
 // Chebyshev step: r = b - A xin; d = c1 d + c2 dinv r; xout = xin + d.
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin,
-                                  T* d, T* xout, const T* dinv, double c1, double c2, int kind);
+                                  T* d, T* xout, const T* dinv, double c1, double c2, int kind, bool il = false);
 // BSR3 strain-form A: y = A x or y = b - A x (b may be null).
 template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b,
                                    int kind = STOKES_KERNEL_SPMV_A);
-// B (1x3 blocks): y = B x;  B^T (3x1 blocks): y = B^T x, optionally scaled per row
-// (y_i = s_i * (B^T x)_i) and / or subtracted from b (y = b - ...) or added into y.
-template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha);
+// B (1x3 blocks): y = b + alpha B x;  B^T (3x1 blocks): y = b + alpha s o (B^T x),
+// s an optional per-row scale (b null: 0). k right-hand sides (1 or 4): x and
+// y hold k blocks component-major (velocity [k][3][nvi], pressure [k][np]).
+template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha,
+                                int k = 1);
 template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* scale,
-                                 const T* b, double alpha);
+                                 const T* b, double alpha, int k = 1);
 // y = b - A x for the BSR3 matrix in double-float arithmetic: A = v32 + v32lo,
 // x = xh + xl (both FP32 pairs), exact FP32 products (FMA TwoProduct) summed
 // with TwoSum; y and b FP64. Relative error ~1e-13 of |A||x| using FP32 units
@@ -461,7 +467,8 @@ void bsr3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float
 // Chebyshev step on a BSR3 operator with a per-component diagonal dinv[3][rows]
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
                                   const T* dinv, double c1, double c2, int kind);
-template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y);
+template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y,
+                                    bool il = false);
 
 void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
 
@@ -576,6 +583,12 @@ template <class T> void sub_ratio(const Exec& ex, size_t n, const double* num, c
 // elementwise y = dinv * x * c (first Chebyshev step from zero: d = x = c D^{-1} b)
 template <class T> void cheb_first(const Exec& ex, size_t n, int nr, const T* dinv, const T* b,
                                    double c, T* d, T* x);
+// the same on node-interleaved vectors (row i's nr values at i * nr)
+template <class T> void cheb_first_il(const Exec& ex, size_t n, int nr, const T* dinv, const T* b, double c, T* d,
+                                      T* x);
+// component-major [nr][rows] <-> node-interleaved [rows][nr] (nr = 4 or 12)
+template <class T> void to_interleaved(const Exec& ex, size_t rows, int nr, const T* cm, T* il);
+template <class T> void to_component_major(const Exec& ex, size_t rows, int nr, const T* il, T* cm);
 template <class S, class D> void convert(const Exec& ex, size_t n, const S* x, D* y);
 // hi = FP32(x), lo = FP32(x - hi)
 void split_f64(const Exec& ex, size_t n, const double* x, float* hi, float* lo);

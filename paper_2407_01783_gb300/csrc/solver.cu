@@ -82,9 +82,10 @@ static size_t npres(const stokes_ctx& c) { return (size_t)c.lv[0].np; }
 // ---------------------------------------------------------------------------
 // Chebyshev semi-iteration for D^{-1} M on [lmin, lmax] (Saad, Alg. 12.1)
 // ---------------------------------------------------------------------------
+// il: node-interleaved vectors (several right-hand sides, nr = 4 or 12)
 template <class T>
 static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double lmin, double lmax, int steps,
-                     const T* b, T* x, bool xzero, int kind) {
+                     const T* b, T* x, bool xzero, int kind, bool il = false) {
   // a 3x3-block operator (M.br == 3) has one diagonal entry per component
   const bool block = M.br == 3;
   size_t len = (size_t)M.rows * (block ? 3 : nr);
@@ -97,10 +98,11 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
   if (xzero && (steps - 1) % 2 == 1) std::swap(xa, xb);
   auto step = [&](const T* xin, T* xout, double c1, double c2) {
     if (block) bsr3_cheb<T>(c.ex, M, b, xin, d, xout, dinv, c1, c2, kind);
-    else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind);
+    else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind, il);
   };
   if (xzero) {
-    cheb_first<T>(c.ex, len, block ? 1 : nr, dinv, b, 1.0 / theta, d, xa);
+    if (il) cheb_first_il<T>(c.ex, len, nr, dinv, b, 1.0 / theta, d, xa);
+    else cheb_first<T>(c.ex, len, block ? 1 : nr, dinv, b, 1.0 / theta, d, xa);
   } else {
     step(xa, xb, 0.0, 1.0 / theta);
     std::swap(xa, xb);
@@ -126,7 +128,8 @@ template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int
 // K right-hand sides: 3K (resp. K) component-major components share every
 // sweep of the level matrices
 // ---------------------------------------------------------------------------
-template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K = 1);
+template <class T>
+static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K = 1, bool il = false);
 
 // Levels >= 1 are latency-bound (a few thousand rows per launch), so below
 // level 0 the V-cycle is replayed from a CUDA graph. Graph launches are not
@@ -330,12 +333,14 @@ static const Csr& level_op(const Level& L, int which) { return which == 1 ? L.KQ
 
 // residual r = b - M x of a level operator (scalar with nr components or 3x3 blocks)
 template <class T>
-static void level_resid(stokes_ctx& c, const Csr& M, int nr, const T* b, const T* x, T* r, int kind) {
+static void level_resid(stokes_ctx& c, const Csr& M, int nr, const T* b, const T* x, T* r, int kind, bool il = false) {
   if (M.br == 3) bsr3_apply<T>(c.ex, M, x, r, b, kind);
-  else spmv_resid<T>(c.ex, M, nr, b, x, r, kind);
+  else spmv_resid<T>(c.ex, M, nr, b, x, r, kind, il);
 }
 
-template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K) {
+// il: node-interleaved level vectors (K > 1)
+template <class T>
+static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K, bool il) {
   SK_REQUIRE(which != 2 || K == 1, STOKES_ERR_ARG, "block V-cycle: one right-hand side per call");
   Level& L = c.lv[l];
   const int nr = (which == 1 ? 1 : 3) * K;
@@ -347,7 +352,7 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
       return;
     }
     const T* Minv = which ? pick<T>(L.KQ_cinv64, L.KQ_cinv32) : pick<T>(L.A3_cinv64, L.A3_cinv32);
-    dense_apply<T>(c.ex, Minv, M.rows, nr, b, x);
+    dense_apply<T>(c.ex, Minv, M.rows, nr, b, x, il);
     return;
   }
   const T* dinv = which == 1 ? pick<T>(L.KQ_dinv64, L.KQ_dinv32)
@@ -356,7 +361,7 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
   double lmax = c.opt.cheb_high * lhat, lmin = c.opt.cheb_low * lhat;
   int deg = std::max(1, c.opt.cheb_degree);
   const int kind = which == 1 ? STOKES_KERNEL_SPMV_P1 : (l == 0 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMM_A3_COARSE);
-  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind, il);
   Level& Lc = c.lv[l + 1];
   const Csr& Mc = level_op(Lc, which);
   size_t lenc = (size_t)Mc.rows * nr;
@@ -385,16 +390,29 @@ template <class T> static void vcycle(stokes_ctx& c, int which, int l, const T* 
     spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, (const T*)G.x, x, STOKES_KERNEL_TRANSFER);
   } else {
     Tmp<T> r(c.pool, len);
-    level_resid<T>(c, M, nr, b, x, r, kind);
+    level_resid<T>(c, M, nr, b, x, r, kind, il);
     Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);
-    spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER);
-    vcycle<T>(c, which, l + 1, bc, xc, true, K);
-    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER);
+    spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER, il);
+    vcycle<T>(c, which, l + 1, bc, xc, true, K, il);
+    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER, il);
   }
-  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind, il);
 }
 
+// K > 1: the cycles run on node-interleaved copies (a row's 3K or K values
+// contiguous, gathered as 16-byte vectors by the sparse kernels); b and x
+// stay component-major K-blocks
 template <class T> static void vcycles_plain(stokes_ctx& c, int which, const T* b, T* x, int cycles, int K = 1) {
+  if (K > 1) {
+    const size_t rows = (size_t)level_op(c.lv[0], which).rows;
+    const int nr = (which == 1 ? 1 : 3) * K;
+    Tmp<T> bi(c.pool, rows * nr), xi(c.pool, rows * nr);
+    to_interleaved<T>(c.ex, rows, nr, b, bi);
+    vcycle<T>(c, which, 0, bi, xi, true, K, true);
+    for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, bi, xi, false, K, true);
+    to_component_major<T>(c.ex, rows, nr, xi, x);
+    return;
+  }
   vcycle<T>(c, which, 0, b, x, true, K);
   for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, b, x, false, K);
 }
@@ -1113,13 +1131,22 @@ template <class T> static void project_mean_k(stokes_ctx& c, T* r, size_t n, int
 }
 
 // per-system B and B^T products: y_k = b_k + alpha B x_k; y_k = b_k + alpha s o (B^T x_k)
+// (four systems: one product that reads the matrix once)
 template <class T> static void b_apply_k(stokes_ctx& c, int K, const T* x, T* y, const T* b, double alpha) {
   const size_t nv = nvel(c), np = npres(c);
+  if (K == 4) {
+    b_apply<T>(c.ex, c.B, x, y, b, alpha, 4);
+    return;
+  }
   for (int k = 0; k < K; ++k) b_apply<T>(c.ex, c.B, x + k * nv, y + k * np, b ? b + k * np : nullptr, alpha);
 }
 template <class T>
 static void bt_apply_k(stokes_ctx& c, int K, const T* x, T* y, const T* scale, const T* b, double alpha) {
   const size_t nv = nvel(c), np = npres(c);
+  if (K == 4) {
+    bt_apply<T>(c.ex, c.Bt, x, y, scale, b, alpha, 4);
+    return;
+  }
   for (int k = 0; k < K; ++k)
     bt_apply<T>(c.ex, c.Bt, x + k * np, y + k * nv, scale, b ? b + k * nv : nullptr, alpha);
 }
@@ -1250,11 +1277,9 @@ template <class T> static int cprec_body_k(stokes_ctx& c, int K, const T* r, T* 
       c, np, K,
       [&](const T* p, T* y, double* dq) {
         if (lumped) {
-          Tmp<T> t(c.pool, nv);
-          for (int k = 0; k < K; ++k) {
-            bt_apply<T>(c.ex, c.Bt, p + k * np, t, linv, (const T*)nullptr, 1.0);
-            b_apply<T>(c.ex, c.B, t, y + k * np, (const T*)nullptr, 1.0);
-          }
+          Tmp<T> t(c.pool, (size_t)K * nv);
+          bt_apply_k<T>(c, K, p, t, linv, (const T*)nullptr, 1.0);
+          b_apply_k<T>(c, K, t, y, (const T*)nullptr, 1.0);
         } else if (vmass) {
           Tmp<T> t(c.pool, nv), w(c.pool, nv);
           for (int k = 0; k < K; ++k) {

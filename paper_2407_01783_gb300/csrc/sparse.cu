@@ -86,6 +86,7 @@ ProfScope::~ProfScope() {
 // r * ns + i (ns = number of rows of the vector).
 template <class T, int NR> struct EpiStore {
   static constexpr int nr = NR;
+  static constexpr bool il = false;
   T* y;
   size_t ns;
   __device__ __forceinline__ void operator()(int row, const T* acc) const {
@@ -95,6 +96,7 @@ template <class T, int NR> struct EpiStore {
 };
 template <class T, int NR> struct EpiAdd {
   static constexpr int nr = NR;
+  static constexpr bool il = false;
   T* y;
   size_t ns;
   __device__ __forceinline__ void operator()(int row, const T* acc) const {
@@ -103,7 +105,8 @@ template <class T, int NR> struct EpiAdd {
   }
 };
 template <class T, int NR> struct EpiResid {
-  static constexpr int nr = NR;  // y = b - acc
+  static constexpr int nr = NR;
+  static constexpr bool il = false;  // y = b - acc
   const T* b;
   T* y;
   size_t ns;
@@ -113,7 +116,8 @@ template <class T, int NR> struct EpiResid {
   }
 };
 template <class T, int NR> struct EpiAxpy {
-  static constexpr int nr = NR;  // y = (b ? b : 0) + alpha * s_row * acc
+  static constexpr int nr = NR;
+  static constexpr bool il = false;  // y = (b ? b : 0) + alpha * s_row * acc
   const T* b;
   const T* s;
   T* y;
@@ -133,6 +137,7 @@ template <class T, int NR> struct EpiAxpy {
 // r = b - A x_in; d = c1 d + c2 D^{-1} r; x_out = x_in + d.
 template <class T, int NR> struct EpiCheb {
   static constexpr int nr = NR;
+  static constexpr bool il = false;
   const T* b;
   const T* xin;
   T* d;
@@ -156,6 +161,7 @@ template <class T, int NR> struct EpiCheb {
 // Same step with a diagonal per component (3x3-block operators): dinv[r*ns+row]
 template <class T> struct EpiCheb3 {
   static constexpr int nr = 3;
+  static constexpr bool il = false;
   const T* b;
   const T* xin;
   T* d;
@@ -172,6 +178,98 @@ template <class T> struct EpiCheb3 {
       d[i] = dn;
       xout[i] = xin[i] + dn;
     }
+  }
+};
+
+// Node-interleaved vectors (the V-cycles of several right-hand sides):
+// component r of row i at i * NR + r, so one row's NR values are contiguous
+// and move as 16-byte vectors (NR a multiple of 4 for FP32, of 2 for FP64).
+template <class T, int NR> __device__ __forceinline__ void ldv(const T* __restrict__ p, T* o) {
+  if constexpr (std::is_same<T, float>::value && NR % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NR / 4; ++i) {
+      const float4 v = reinterpret_cast<const float4*>(p)[i];
+      o[4 * i] = v.x, o[4 * i + 1] = v.y, o[4 * i + 2] = v.z, o[4 * i + 3] = v.w;
+    }
+  } else if constexpr (std::is_same<T, double>::value && NR % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NR / 2; ++i) {
+      const double2 v = reinterpret_cast<const double2*>(p)[i];
+      o[2 * i] = v.x, o[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NR; ++i) o[i] = p[i];
+  }
+}
+template <class T, int NR> __device__ __forceinline__ void stv(T* __restrict__ p, const T* o) {
+  if constexpr (std::is_same<T, float>::value && NR % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NR / 4; ++i)
+      reinterpret_cast<float4*>(p)[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+  } else if constexpr (std::is_same<T, double>::value && NR % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NR / 2; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(o[2 * i], o[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NR; ++i) p[i] = o[i];
+  }
+}
+template <class T, int NR> struct EpiStoreIL {
+  static constexpr int nr = NR;
+  static constexpr bool il = true;
+  T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const { stv<T, NR>(y + (size_t)row * NR, acc); }
+};
+template <class T, int NR> struct EpiAddIL {
+  static constexpr int nr = NR;
+  static constexpr bool il = true;
+  T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    T v[NR];
+    ldv<T, NR>(y + (size_t)row * NR, v);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] += acc[r];
+    stv<T, NR>(y + (size_t)row * NR, v);
+  }
+};
+template <class T, int NR> struct EpiResidIL {
+  static constexpr int nr = NR;
+  static constexpr bool il = true;
+  const T* b;
+  T* y;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    T v[NR];
+    ldv<T, NR>(b + (size_t)row * NR, v);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] -= acc[r];
+    stv<T, NR>(y + (size_t)row * NR, v);
+  }
+};
+template <class T, int NR> struct EpiChebIL {
+  static constexpr int nr = NR;
+  static constexpr bool il = true;
+  const T* b;
+  const T* xin;
+  T* d;
+  T* xout;
+  const T* dinv;
+  T c1, c2;
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    const T di = dinv[row];
+    const size_t o = (size_t)row * NR;
+    T bv[NR], dv[NR], xv[NR];
+    ldv<T, NR>(b + o, bv);
+    ldv<T, NR>(d + o, dv);
+    ldv<T, NR>(xin + o, xv);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T dn = c1 * dv[r] + c2 * di * (bv[r] - acc[r]);
+      dv[r] = dn;
+      xv[r] += dn;
+    }
+    stv<T, NR>(d + o, dv);
+    stv<T, NR>(xout + o, xv);
   }
 };
 
@@ -220,10 +318,15 @@ __global__ void __launch_bounds__(256) k_csr(int rows, const int* __restrict__ r
         a[u] = ok ? av : T(0);
       }
       T xv[U][NR];
+      if constexpr (Epi::il) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) ldv<T, NR>(x + (size_t)c[u] * NR, xv[u]);
+      } else {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) xv[u][r] = x[r * xs + c[u]];
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) xv[u][r] = x[r * xs + c[u]];
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -449,15 +552,18 @@ int bsr3_dot_grid(const Csr& m) {
   return std::min(cdiv((long long)m.rows * 32, 256), 8 * sms);
 }
 
-// 1x3 blocks: B (P1 rows, interior P2 node columns)
-template <int G, class T, class Epi>
+// 1x3 blocks: B (P1 rows, interior P2 node columns), for K right-hand sides
+// (x: 3K component-major components, y: K); the matrix is read once for all
+template <int G, int K, class T, class Epi>
 __global__ void __launch_bounds__(256) k_b(int rows, const int* __restrict__ rp, const int* __restrict__ col,
                                            const T* __restrict__ v, long long nnz, const T* __restrict__ x, size_t xs,
                                            Epi epi) {
   constexpr int U = Batch<G>::U;
   int gt = blockIdx.x * blockDim.x + threadIdx.x;
   int row = gt / G, lane = gt & (G - 1);
-  T acc[1] = {T(0)};
+  T acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = T(0);
   if (row < rows) {
     const int e = rp[row + 1];
     for (int k = rp[row] + lane; k < e; k += U * G) {
@@ -476,24 +582,30 @@ __global__ void __launch_bounds__(256) k_b(int rows, const int* __restrict__ rp,
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        acc[0] += a[u][0] * x[c[u]] + a[u][1] * x[xs + c[u]] + a[u][2] * x[2 * xs + c[u]];
-      }
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const T* xq = x + (size_t)3 * q * xs;
+          acc[q] += a[u][0] * xq[c[u]] + a[u][1] * xq[xs + c[u]] + a[u][2] * xq[2 * xs + c[u]];
+        }
     }
   }
-  group_reduce<G, T, 1>(acc);
+  group_reduce<G, T, K>(acc);
   if (row < rows && lane == 0) epi(row, acc);
 }
 
-// 3x1 blocks: B^T (interior P2 node rows, P1 columns)
-template <int G, class T, class Epi>
+// 3x1 blocks: B^T (interior P2 node rows, P1 columns), for K right-hand sides
+// (x: K components, y: 3K component-major components)
+template <int G, int K, class T, class Epi>
 __global__ void __launch_bounds__(256) k_bt(int rows, const int* __restrict__ rp, const int* __restrict__ col,
                                             const T* __restrict__ v, long long nnz, const T* __restrict__ x, size_t xs,
                                             Epi epi) {
   constexpr int U = Batch<G>::U;
   int gt = blockIdx.x * blockDim.x + threadIdx.x;
   int row = gt / G, lane = gt & (G - 1);
-  T acc[3] = {T(0), T(0), T(0)};
+  T acc[3 * K];
+#pragma unroll
+  for (int q = 0; q < 3 * K; ++q) acc[q] = T(0);
   if (row < rows) {
     const int e = rp[row + 1];
     for (int k = rp[row] + lane; k < e; k += U * G) {
@@ -512,14 +624,16 @@ __global__ void __launch_bounds__(256) k_bt(int rows, const int* __restrict__ rp
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const T xv = x[c[u]];
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) acc[j] += a[u][j] * xv;
-      }
+        for (int q = 0; q < K; ++q) {
+          const T xv = x[(size_t)q * xs + c[u]];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc[3 * q + j] += a[u][j] * xv;
+        }
     }
   }
-  group_reduce<G, T, 3>(acc);
+  group_reduce<G, T, 3 * K>(acc);
   if (row < rows && lane == 0) epi(row, acc);
 }
 
@@ -573,10 +687,20 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
     size_t cc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) cc[j] = (size_t)min(max(row + a.lin[db + 4 * e4 + j], 0), last);
+    if constexpr (Epi::il) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < 4; ++j) {
+        T xv[NR];
+        ldv<T, NR>(x + cc[j] * NR, xv);
 #pragma unroll
-      for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * x[q * xs + cc[j]];
+        for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * xv[q];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * x[q * xs + cc[j]];
+    }
   }
   epi(row, acc);
 }
@@ -625,12 +749,14 @@ static void launch_g(const Exec& ex, const Csr& m, Shape sh, const T* x, const E
         k_bsr3<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
       break;
     case SH_B:
-      if constexpr (Epi::nr == 1)
-        k_b<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
+      if constexpr (Epi::nr == 1 || Epi::nr == 4)
+        k_b<G, Epi::nr, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols,
+                                                       epi);
       break;
     case SH_BT:
-      if constexpr (Epi::nr == 3)
-        k_bt<G, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x, m.cols, epi);
+      if constexpr (Epi::nr == 3 || Epi::nr == 12)
+        k_bt<G, Epi::nr / 3, T, Epi><<<grid, bs, 0, ex.s>>>(m.rows, m.rowptr, m.col, m.template v<T>(), m.nnz, x,
+                                                            m.cols, epi);
       break;
   }
   SK_CHECK_LAUNCH();
@@ -666,38 +792,55 @@ template <class F> static void with_nr(int nr, F&& f) {
   }
 }
 
-template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
+// il: node-interleaved vectors (NR = 4 or 12 only), else component-major
+template <int NR> static constexpr bool il_ok() { return NR % 4 == 0; }
+static void require_il(int nr, bool il) {
+  SK_REQUIRE(!il || nr % 4 == 0, STOKES_ERR_ARG, "interleaved vectors need 4 or 12 components");
+}
+template <class T, class E> static void run_scalar(const Exec& ex, const Csr& m, bool st, const T* x, const E& e) {
+  if (st) launch_stencil(ex, *m.st, E::nr, x, e);
+  else launch(ex, m, SH_CSR, x, e, m.group);
+}
+template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il) {
+  require_il(nr, il);
   const bool st = use_stencil<T>(m);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 0) : prod_bytes(m, sizeof(T), nr, nr, 0));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
-    const EpiStore<T, NR> e{y, (size_t)m.rows};
-    if (st) launch_stencil(ex, *m.st, NR, x, e);
-    else launch(ex, m, SH_CSR, x, e, m.group);
+    if constexpr (il_ok<NR>()) {
+      if (il) return run_scalar(ex, m, st, x, EpiStoreIL<T, NR>{y});
+    }
+    run_scalar(ex, m, st, x, EpiStore<T, NR>{y, (size_t)m.rows});
   });
 }
-template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind) {
+template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il) {
+  require_il(nr, il);
   const bool st = use_stencil<T>(m);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
-    const EpiAdd<T, NR> e{y, (size_t)m.rows};
-    if (st) launch_stencil(ex, *m.st, NR, x, e);
-    else launch(ex, m, SH_CSR, x, e, m.group);
+    if constexpr (il_ok<NR>()) {
+      if (il) return run_scalar(ex, m, st, x, EpiAddIL<T, NR>{y});
+    }
+    run_scalar(ex, m, st, x, EpiAdd<T, NR>{y, (size_t)m.rows});
   });
 }
-template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind) {
+template <class T>
+void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind, bool il) {
+  require_il(nr, il);
   const bool st = use_stencil<T>(m);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
-    const EpiResid<T, NR> e{b, y, (size_t)m.rows};
-    if (st) launch_stencil(ex, *m.st, NR, x, e);
-    else launch(ex, m, SH_CSR, x, e, m.group);
+    if constexpr (il_ok<NR>()) {
+      if (il) return run_scalar(ex, m, st, x, EpiResidIL<T, NR>{b, y});
+    }
+    run_scalar(ex, m, st, x, EpiResid<T, NR>{b, y, (size_t)m.rows});
   });
 }
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin, T* d, T* xout,
-                                  const T* dinv, double c1, double c2, int kind) {
+                                  const T* dinv, double c1, double c2, int kind, bool il) {
+  require_il(nr, il);
   const bool st = use_stencil<T>(m);
   // streams: b, x_in (own row), d read, d write, x_out write, dinv
   ProfScope ps(ex, kind,
@@ -705,9 +848,10 @@ template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T*
                    (double)sizeof(T) * m.rows);
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
-    const EpiCheb<T, NR> e{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows};
-    if (st) launch_stencil(ex, *m.st, NR, xin, e);
-    else launch(ex, m, SH_CSR, xin, e, m.group);
+    if constexpr (il_ok<NR>()) {
+      if (il) return run_scalar(ex, m, st, xin, EpiChebIL<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2});
+    }
+    run_scalar(ex, m, st, xin, EpiCheb<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
   });
 }
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
@@ -753,21 +897,27 @@ template <class T> bool bsr3_apply_dot(const Exec& ex, const Csr& m, const T* x,
   return false;
 }
 
-template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha) {
-  ProfScope ps(ex, STOKES_KERNEL_B, m.bytes(sizeof(T)) + sizeof(T) * (3.0 * m.cols + m.rows * (b ? 2.0 : 1.0)));
-  launch(ex, m, SH_B, x, EpiAxpy<T, 1>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group);
+template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha, int k) {
+  SK_REQUIRE(k == 1 || k == 4, STOKES_ERR_ARG, "B product: 1 or 4 right-hand sides");
+  ProfScope ps(ex, STOKES_KERNEL_B, m.bytes(sizeof(T)) + sizeof(T) * k * (3.0 * m.cols + m.rows * (b ? 2.0 : 1.0)));
+  if (k == 4) launch(ex, m, SH_B, x, EpiAxpy<T, 4>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group);
+  else launch(ex, m, SH_B, x, EpiAxpy<T, 1>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group);
 }
 template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* scale, const T* b,
-                                 double alpha) {
-  ProfScope ps(ex, STOKES_KERNEL_BT, m.bytes(sizeof(T)) + sizeof(T) * (1.0 * m.cols + 3.0 * m.rows * (b ? 2.0 : 1.0) +
-                                                                       (scale ? m.rows : 0)));
-  launch(ex, m, SH_BT, x, EpiAxpy<T, 3>{b, scale, y, (T)alpha, (size_t)m.rows}, m.group);
+                                 double alpha, int k) {
+  SK_REQUIRE(k == 1 || k == 4, STOKES_ERR_ARG, "B^T product: 1 or 4 right-hand sides");
+  ProfScope ps(ex, STOKES_KERNEL_BT,
+               m.bytes(sizeof(T)) +
+                   sizeof(T) * (k * (1.0 * m.cols + 3.0 * m.rows * (b ? 2.0 : 1.0)) + (scale ? m.rows : 0)));
+  if (k == 4) launch(ex, m, SH_BT, x, EpiAxpy<T, 12>{b, scale, y, (T)alpha, (size_t)m.rows}, m.group);
+  else launch(ex, m, SH_BT, x, EpiAxpy<T, 3>{b, scale, y, (T)alpha, (size_t)m.rows}, m.group);
 }
 
 // coarse dense inverse applied to NR right-hand sides: one warp per row
-template <int NR, class T>
+template <int NR, class T, bool IL = false>
 __global__ void k_dense(const T* __restrict__ M, int m, const T* __restrict__ b, T* __restrict__ y) {
   // component-major right-hand sides: component r of row j at r * m + j
+  // (IL: node-interleaved, at j * NR + r)
   int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (row >= m) return;
@@ -777,7 +927,7 @@ __global__ void k_dense(const T* __restrict__ M, int m, const T* __restrict__ b,
   for (int j = lane; j < m; j += 32) {
     T a = M[(size_t)row * m + j];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] += a * b[(size_t)r * m + j];
+    for (int r = 0; r < NR; ++r) acc[r] += a * b[IL ? (size_t)j * NR + r : (size_t)r * m + j];
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1)
@@ -785,13 +935,17 @@ __global__ void k_dense(const T* __restrict__ M, int m, const T* __restrict__ b,
     for (int r = 0; r < NR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
   if (lane == 0)
 #pragma unroll
-    for (int r = 0; r < NR; ++r) y[(size_t)r * m + row] = acc[r];
+    for (int r = 0; r < NR; ++r) y[IL ? (size_t)row * NR + r : (size_t)r * m + row] = acc[r];
 }
 
-template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y) {
+template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y, bool il) {
   ProfScope ps(ex, STOKES_KERNEL_OTHER, (double)sizeof(T) * ((double)m * m + 2.0 * m * nr));
   int grid = cdiv(m, 8);
-  with_nr(nr, [&](auto NRc) { k_dense<decltype(NRc)::value, T><<<grid, 256, 0, ex.s>>>(Minv, m, b, y); });
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    if (il) k_dense<NR, T, true><<<grid, 256, 0, ex.s>>>(Minv, m, b, y);
+    else k_dense<NR, T, false><<<grid, 256, 0, ex.s>>>(Minv, m, b, y);
+  });
   SK_CHECK_LAUNCH();
 }
 
@@ -913,16 +1067,16 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
 }
 
 #define SK_INST(T)                                                                                        \
-  template void spmv_store<T>(const Exec&, const Csr&, int, const T*, T*, int);                          \
-  template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int);                            \
-  template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int);                \
+  template void spmv_store<T>(const Exec&, const Csr&, int, const T*, T*, int, bool);                          \
+  template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int, bool);                            \
+  template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int, bool);                \
   template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
-                             double, int);                                                                     \
+                             double, int, bool);                                                                     \
   template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, int);                          \
   template void bsr3_cheb<T>(const Exec&, const Csr&, const T*, const T*, T*, T*, const T*, double, double, int); \
-  template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double);                     \
-  template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double);          \
-  template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*);                          \
+  template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double, int);                \
+  template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double, int);     \
+  template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*, bool);                    \
   template bool bsr3_apply_dot<T>(const Exec&, const Csr&, const T*, T*, const DotScratch&, double*);
 SK_INST(float)
 SK_INST(double)
