@@ -237,9 +237,11 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   if (c.opt.format != 1) {
     auto add = [&](Csr& m, int p2, int nn) {
       const int min_rows = c.opt.stencil_min_rows > 0 ? c.opt.stencil_min_rows : kStencilMinRows;
-      if ((c.opt.format == 0 || c.opt.format == 3) && m.rows < min_rows) return;
+      const bool by_size = c.opt.format == 0 || c.opt.format == 3;
+      if (by_size && m.rows < std::min(min_rows, kStencilMinRowsIL)) return;
       c.stencils.emplace_back(stencil_from_csr(c.ex, c.arena, st, p2, nn, m));
       m.st = c.stencils.back().get();
+      m.st_min_single = by_size ? min_rows : 0;
     };
     for (Level& L : c.lv) {
       add(L.A3, 1, L.n);

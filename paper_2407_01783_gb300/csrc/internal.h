@@ -244,7 +244,9 @@ struct Csr {
   float* v32 = nullptr;
   float* v32lo = nullptr;  // v64 - v32 rounded to FP32 (double-float residual), or null
   int group = 8;  // threads per row
-  const StencilOp* st = nullptr;  // same matrix in stencil storage (used when set)
+  const StencilOp* st = nullptr;  // same matrix in stencil storage (used when set, see st_min_single)
+  int st_min_single = 0;          // component-major products (one right-hand side) use the stencil
+                                  // storage only on matrices with at least this many rows
   const Sym3Op* sym = nullptr;    // 3x3-block matrix in symmetric stencil storage: used for the
                                   // double-float residual, and for all products if sym_products
   bool sym_products = false;
@@ -538,6 +540,12 @@ template <class T> bool bsr3_apply_dot(const Exec& ex, const Csr& m, const T* x,
 // dot x . (A x); double-float residual y = b - A x
 template <class T> void sym3_launch(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, const DotScratch* ds,
                                     double* dot);
+// the same (no dot) for four right-hand sides [4][3][rows] in one sweep
+template <class T> void sym3_launch4(const Exec& ex, const Csr& m, const T* x, T* y, const T* b);
+// k right-hand sides of the BSR3 operator (x, y, b: [k][3][rows]): one sweep
+// for k = 4 with symmetric storage, else one product per right-hand side
+template <class T> void bsr3_apply_k(const Exec& ex, const Csr& m, int k, const T* x, T* y, const T* b,
+                                     int kind = STOKES_KERNEL_SPMV_A);
 void sym3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y);
 double sym3_bytes(const Sym3Op& so, int esz, int rows, int streams);
 // most blocks of one symmetric-stencil product launch (fused-dot partial capacity)
@@ -551,6 +559,10 @@ constexpr size_t kCompensatedMin = (size_t)1 << 20;
 // Stencil storage is used on levels with at least this many rows; smaller
 // grids are latency-bound with one thread per row and stay CSR.
 constexpr int kStencilMinRows = 1 << 18;
+// With several right-hand sides (node-interleaved vectors, 4 or 12 values per
+// row) a row carries enough work that the stencil kernel already pays from
+// this size on.
+constexpr int kStencilMinRowsIL = 1 << 15;
 // out[i] = sum_j x_i[j] * y_i[j] for i < k (y_i == nullptr means all ones).
 // Accumulation of FP32 dot products: kDotAuto = compensated FP32 partial sums
 // for vectors of at least kCompensatedMin entries, kDotFast = compensated for

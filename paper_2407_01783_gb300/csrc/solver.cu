@@ -119,8 +119,16 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
 // M_Q^{-1} b by Chebyshev-Jacobi on the exact Wathen interval (K right-hand
 // sides [K][np] in one sweep of M_Q)
 template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int steps, int K = 1) {
-  cheb_run<T>(c, c.MQ, K, pick<T>(c.MQ_dinv64, c.MQ_dinv32), kMassLow, kMassHigh, std::max(1, steps), b, x, true,
-              STOKES_KERNEL_SPMV_P1);
+  const T* dinv = pick<T>(c.MQ_dinv64, c.MQ_dinv32);
+  if (K == 4) {  // on node-interleaved copies (see vcycles_plain)
+    const size_t rows = (size_t)c.MQ.rows;
+    Tmp<T> bi(c.pool, rows * K), xi(c.pool, rows * K);
+    to_interleaved<T>(c.ex, rows, K, b, bi);
+    cheb_run<T>(c, c.MQ, K, dinv, kMassLow, kMassHigh, std::max(1, steps), bi, xi, true, STOKES_KERNEL_SPMV_P1, true);
+    to_component_major<T>(c.ex, rows, K, xi, x);
+    return;
+  }
+  cheb_run<T>(c, c.MQ, K, dinv, kMassLow, kMassHigh, std::max(1, steps), b, x, true, STOKES_KERNEL_SPMV_P1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1154,7 +1162,7 @@ static void bt_apply_k(stokes_ctx& c, int K, const T* x, T* y, const T* scale, c
 // y_k = A_gamma x_k for K velocity blocks
 template <class T> static void op_A_k(stokes_ctx& c, int K, const T* x, T* y) {
   const size_t nv = nvel(c), np = npres(c);
-  for (int k = 0; k < K; ++k) bsr3_apply<T>(c.ex, c.A, x + k * nv, y + k * nv, (const T*)nullptr);
+  bsr3_apply_k<T>(c.ex, c.A, K, x, y, (const T*)nullptr);
   if (c.gamma > 0.0) {
     Tmp<T> bx(c.pool, K * np), mb(c.pool, K * np);
     b_apply_k<T>(c, K, x, bx, (const T*)nullptr, 1.0);

@@ -718,8 +718,8 @@ static void launch_stencil(const Exec& ex, const StencilOp& so, int nr, const T*
   SK_CHECK_LAUNCH();
 }
 
-template <class T> static inline bool use_stencil(const Csr& m) {
-  return m.st != nullptr && m.st->template v<T>() != nullptr;
+template <class T> static inline bool use_stencil(const Csr& m, bool il) {
+  return m.st != nullptr && m.st->template v<T>() != nullptr && (il || m.rows >= m.st_min_single);
 }
 
 // algorithmic bytes: the matrix's stored entries (not the zero padding), x
@@ -803,7 +803,7 @@ template <class T, class E> static void run_scalar(const Exec& ex, const Csr& m,
 }
 template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il) {
   require_il(nr, il);
-  const bool st = use_stencil<T>(m);
+  const bool st = use_stencil<T>(m, il);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 0) : prod_bytes(m, sizeof(T), nr, nr, 0));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
@@ -815,7 +815,7 @@ template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T
 }
 template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il) {
   require_il(nr, il);
-  const bool st = use_stencil<T>(m);
+  const bool st = use_stencil<T>(m, il);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
@@ -828,7 +828,7 @@ template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* 
 template <class T>
 void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind, bool il) {
   require_il(nr, il);
-  const bool st = use_stencil<T>(m);
+  const bool st = use_stencil<T>(m, il);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
@@ -841,7 +841,7 @@ void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T*
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin, T* d, T* xout,
                                   const T* dinv, double c1, double c2, int kind, bool il) {
   require_il(nr, il);
-  const bool st = use_stencil<T>(m);
+  const bool st = use_stencil<T>(m, il);
   // streams: b, x_in (own row), d read, d write, x_out write, dinv
   ProfScope ps(ex, kind,
                (st ? stencil_bytes(*m.st, sizeof(T), nr, 4) : prod_bytes(m, sizeof(T), nr, nr, 4)) +
@@ -869,6 +869,16 @@ template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* 
   ProfScope ps(ex, kind, prod_bytes(m, sizeof(T), 3, 3, b ? 1 : 0));
   if (b) launch(ex, m, SH_BSR3, x, EpiResid<T, 3>{b, y, (size_t)m.rows}, m.group);
   else launch(ex, m, SH_BSR3, x, EpiStore<T, 3>{y, (size_t)m.rows}, m.group);
+}
+template <class T>
+void bsr3_apply_k(const Exec& ex, const Csr& m, int k, const T* x, T* y, const T* b, int kind) {
+  if (k == 4 && m.sym && m.sym->template v<T>() && m.sym_products) {
+    ProfScope ps(ex, kind, (double)m.sym->total * sizeof(T) + (double)sizeof(T) * 3.0 * m.rows * 4 * (b ? 2 : 1));
+    sym3_launch4<T>(ex, m, x, y, b);
+    return;
+  }
+  const size_t len = 3 * (size_t)m.rows;
+  for (int i = 0; i < k; ++i) bsr3_apply<T>(ex, m, x + i * len, y + i * len, b ? b + i * len : nullptr, kind);
 }
 template <class T> bool bsr3_apply_dot(const Exec& ex, const Csr& m, const T* x, T* y, const DotScratch& ds,
                                        double* dot) {
@@ -1077,6 +1087,7 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double, int);                \
   template void bt_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, const T*, double, int);     \
   template void dense_apply<T>(const Exec&, const T*, int, int, const T*, T*, bool);                    \
+  template void bsr3_apply_k<T>(const Exec&, const Csr&, int, const T*, T*, const T*, int);            \
   template bool bsr3_apply_dot<T>(const Exec&, const Csr&, const T*, T*, const DotScratch&, double*);
 SK_INST(float)
 SK_INST(double)

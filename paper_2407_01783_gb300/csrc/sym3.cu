@@ -115,11 +115,13 @@ struct SymBatch {
   static constexpr int U = 8 / G;
 };
 
-// this lane's share of acc[r] = sum over the row's blocks of A(i, j)_{r q} x_j[q],
-// U entries' loads in flight per lane
-template <int G, int U, class T>
+// this lane's share of acc[3k + r] = sum over the row's blocks of
+// A(i, j)_{r q} x_k,j[q] for K right-hand sides (x: 3K component-major
+// components), U entries' loads in flight per lane; each block is read once
+// for all K
+template <int G, int U, int K, class T>
 __device__ __forceinline__ void sym3_row(const Sym3Args& a, const SymRow& R, int lane, const T* __restrict__ v,
-                                         const T* __restrict__ x, size_t xs, T acc[3]) {
+                                         const T* __restrict__ x, size_t xs, T* acc) {
   const int c = R.c;
   const int last = (int)xs - 1;
   const size_t rc = (size_t)a.prows[c];
@@ -141,13 +143,18 @@ __device__ __forceinline__ void sym3_row(const Sym3Args& a, const SymRow& R, int
         w[u][k] = ok ? t : T(0);
       }
     }
-    T xv[U][3];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u][0] = x[cc[u]], xv[u][1] = x[xs + cc[u]], xv[u][2] = x[2 * xs + cc[u]];
+    for (int k = 0; k < K; ++k) {
+      const T* xk = x + (size_t)3 * k * xs;
+      T xv[U][3];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+      for (int u = 0; u < U; ++u) xv[u][0] = xk[cc[u]], xv[u][1] = xk[xs + cc[u]], xv[u][2] = xk[2 * xs + cc[u]];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) acc[r] += w[u][3 * r] * xv[u][0] + w[u][3 * r + 1] * xv[u][1] + w[u][3 * r + 2] * xv[u][2];
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          acc[3 * k + r] += w[u][3 * r] * xv[u][0] + w[u][3 * r + 1] * xv[u][1] + w[u][3 * r + 2] * xv[u][2];
+    }
   }
   const int l0 = a.lbeg[c], nl = a.lbeg[c + 1] - l0;
   for (int e0 = lane; e0 < nl; e0 += U * G) {
@@ -170,13 +177,18 @@ __device__ __forceinline__ void sym3_row(const Sym3Args& a, const SymRow& R, int
         w[u][k] = in ? t : T(0);
       }
     }
-    T xv[U][3];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u][0] = x[cc[u]], xv[u][1] = x[xs + cc[u]], xv[u][2] = x[2 * xs + cc[u]];
+    for (int k = 0; k < K; ++k) {
+      const T* xk = x + (size_t)3 * k * xs;
+      T xv[U][3];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+      for (int u = 0; u < U; ++u) xv[u][0] = xk[cc[u]], xv[u][1] = xk[xs + cc[u]], xv[u][2] = xk[2 * xs + cc[u]];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) acc[r] += w[u][r] * xv[u][0] + w[u][3 + r] * xv[u][1] + w[u][6 + r] * xv[u][2];
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          acc[3 * k + r] += w[u][r] * xv[u][0] + w[u][3 + r] * xv[u][1] + w[u][6 + r] * xv[u][2];
+    }
   }
 }
 
@@ -184,24 +196,29 @@ __device__ __forceinline__ void sym3_row(const Sym3Args& a, const SymRow& R, int
 // Blocks walk the virtual blocks (plane order) with a grid stride; the dot
 // variant runs one resident wave so that its grid sum takes one counter
 // increment per resident block.
-template <int G, int U, class T, bool DOT>
+// K right-hand sides: x, b, y hold 3K component-major components (the dot
+// variant is K = 1 only)
+template <int G, int U, class T, bool DOT, int K = 1>
 __global__ void __launch_bounds__(kSymBlock) k_sym3(const Sym3Args a, int nvb, const T* __restrict__ v,
                                                    const T* __restrict__ x, size_t xs, const T* __restrict__ b,
                                                    T* __restrict__ y, double* partial, unsigned* counter,
                                                    double* dot) {
+  static_assert(!DOT || K == 1, "fused dot: one right-hand side");
   const int lane = (int)threadIdx.x % G;
   double part = 0.0;
   for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
     const SymRow R = sym3_locate<G>(a, vb);
-    T acc[3] = {T(0), T(0), T(0)};
-    if (R.valid) sym3_row<G, U, T>(a, R, lane, v, x, xs, acc);
+    T acc[3 * K];
+#pragma unroll
+    for (int r = 0; r < 3 * K; ++r) acc[r] = T(0);
+    if (R.valid) sym3_row<G, U, K, T>(a, R, lane, v, x, xs, acc);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+      for (int r = 0; r < 3 * K; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     if (R.valid && lane == 0) {
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
+      for (int r = 0; r < 3 * K; ++r) {
         const size_t i = r * xs + R.row;
         y[i] = b ? b[i] - acc[r] : acc[r];
         if (DOT) part += (double)(acc[r] * x[i]);
@@ -343,6 +360,27 @@ static void sym3_launch_g(const Exec& ex, const Csr& m, const T* x, T* y, const 
   SK_CHECK_LAUNCH();
 }
 
+// four right-hand sides (x, y, b: [4][3][rows]): every stored block read once
+// for the four; one thread per row, two entries' loads in flight
+template <class T> void sym3_launch4(const Exec& ex, const Csr& m, const T* x, T* y, const T* b) {
+  const Sym3Op& so = *m.sym;
+  const Sym3Args a = sym3_args(so, 1);
+  const int nvb = sym3_blocks(so, a);
+  if (nvb == 0) return;
+  static thread_local int w = 0;
+  if (!w) {
+    int dev = 0, sms = 0, occ = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym3<1, 2, T, false, 4>, kSymBlock, 0));
+    w = std::max(1, sms * std::max(1, occ));
+  }
+  const int grid = std::min(nvb, w);
+  k_sym3<1, 2, T, false, 4><<<grid, kSymBlock, 0, ex.s>>>(a, nvb, so.template v<T>(), x, (size_t)m.rows, b, y, nullptr,
+                                                       nullptr, nullptr);
+  SK_CHECK_LAUNCH();
+}
+
 template <class T>
 void sym3_launch(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, const DotScratch* ds, double* dot) {
   // (threads per row, entries in flight per lane)
@@ -377,6 +415,8 @@ void sym3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float
 
 template void sym3_launch<float>(const Exec&, const Csr&, const float*, float*, const float*, const DotScratch*,
                                  double*);
+template void sym3_launch4<float>(const Exec&, const Csr&, const float*, float*, const float*);
+template void sym3_launch4<double>(const Exec&, const Csr&, const double*, double*, const double*);
 template void sym3_launch<double>(const Exec&, const Csr&, const double*, double*, const double*, const DotScratch*,
                                   double*);
 
