@@ -199,17 +199,19 @@ stokes_status stokes_solve(stokes_ctx* ctx, const double* f, const double* g,
 
 /* k systems with the same operator (Eq. Saddle_point_A_BT_B, k right-hand
  * sides): f device [k][(2n+1)^3][3], g device [k][(n+1)^3] or NULL, u device
- * [k][(2n+1)^3][3], p device [k][(n+1)^3], info NULL or an array of k. With
- * Method 2 the systems are solved four at a time in lockstep (FGMRES of Sec.
- * 2.4 per system, each with its own Krylov basis, Hessenberg matrix and
- * convergence test): every V-cycle, Chebyshev mass inverse and vector kernel
- * sweeps its matrix and launches once for the four systems. A last group of
- * two or three systems is padded with zero systems, a single one takes the
- * stokes_solve path; Method 1 solves the systems one after another. Each
- * system meets tol on its own full residual (info[i].rel_residual);
- * info[i].outer_iters counts the iterations system i took part in. Returns
- * STOKES_OK if every system converged, else the first failing status. A
- * following stokes_adjoint uses the last system's solution. 1 <= k <= 4096. */
+ * [k][(2n+1)^3][3], p device [k][(n+1)^3], info NULL or an array of k. The
+ * systems are solved four at a time in lockstep, each with its own Krylov
+ * coefficients and convergence test (Method 1: flexible Schur CG of Sec. 2.3
+ * with lockstep inner PCG; Method 2: FGMRES of Sec. 2.4 with its own basis
+ * and Hessenberg matrix per system): every V-cycle, Chebyshev mass inverse,
+ * product with A, B or B^T and vector kernel sweeps its matrix and launches
+ * once for the four systems. A last group of two or three systems is padded
+ * with zero systems; a single one takes the stokes_solve path. Each system
+ * meets tol on its own full residual (info[i].rel_residual);
+ * info[i].outer_iters counts the outer iterations system i took part in.
+ * Returns STOKES_OK if every system converged, else the first failing status.
+ * A following stokes_adjoint uses the last system's solution.
+ * 1 <= k <= 4096. */
 stokes_status stokes_solve_multi(stokes_ctx* ctx, int k, const double* f, const double* g,
                                  double tol, double* u, double* p, stokes_info* info);
 

@@ -690,6 +690,8 @@ template <class T> void kmdot(const Exec& ex, const DotScratch& ds, size_t nu, s
                               const T* const* V, const T* w, double* out, int ld);
 template <class T> void kmaxpy(const Exec& ex, size_t nu, size_t np, int K, int J, const T* const* V, const double* h,
                                const double* hhost, int ld, double sign, T* w);
+// out[k] = a[k] - b[k] for k < K (device scalars)
+void ksub(const Exec& ex, int K, double* out, const double* a, const double* b);
 // scratch doubles the K-dot kernels need (capacity of DotScratch::k_partial)
 long long kdot_scratch(size_t len_max, int K);
 void expand_velocity(const Exec& ex, int n, const double* ured, double* uall);

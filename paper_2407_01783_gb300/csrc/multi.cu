@@ -143,6 +143,11 @@ __global__ void __launch_bounds__(256) k_kmaxpy(KSeg s, KBasis<T> V, int J, cons
   }
 }
 
+__global__ void k_ksub(int K, double* out, const double* a, const double* b) {
+  const int k = threadIdx.x;
+  if (k < K) out[k] = a[k] - b[k];
+}
+
 // ---------------------------------------------------------------------------
 // host wrappers
 // ---------------------------------------------------------------------------
@@ -238,6 +243,13 @@ void kmaxpy(const Exec& ex, size_t nu, size_t np, int K, int J, const T* const* 
     case 16: k_kmaxpy<T, 16><<<grid, 256, 0, ex.s>>>(sg, B, J, h, hc, ld, sign, w); break;
     default: k_kmaxpy<T, 32><<<grid, 256, 0, ex.s>>>(sg, B, J, h, hc, ld, sign, w); break;
   }
+  SK_CHECK_LAUNCH();
+}
+
+void ksub(const Exec& ex, int K, double* out, const double* a, const double* b) {
+  SK_REQUIRE(K >= 1 && K <= kMaxRhs, STOKES_ERR_ARG, "ksub: 1 to 8 values");
+  ProfScope ps(ex, STOKES_KERNEL_OTHER, 24.0 * K);
+  k_ksub<<<1, 32, 0, ex.s>>>(K, out, a, b);
   SK_CHECK_LAUNCH();
 }
 

@@ -1347,6 +1347,99 @@ template <class T> static void block_prec_k(stokes_ctx& c, int K, const T* v, T*
   }
 }
 
+// Method 1 (flexible CG on the Schur complement, as method1()) for the K
+// systems of the residual K-vector R into the K-vector X, in lockstep: each
+// system keeps its own alpha, beta and stopping test; the inner A-solves run
+// as one lockstep PCG whose systems stop on their own tolerances. A system
+// that has converged gets a zero search direction, so its inner solves
+// return at once. Arguments as method2_k().
+template <class T>
+static void method1_k(stokes_ctx& c, int K, const T* R, T* X, const double* eta, double tol_in, unsigned live,
+                      int* its) {
+  const size_t nv = nvel(c), np = npres(c), Kv = (size_t)K * nv, Kp = (size_t)K * np;
+  T* dU = X;
+  T* dP = X + Kv;
+  const T* rg = R + Kv;
+  Tmp<T> Fg(c.pool, c.gamma > 0.0 ? Kv : 1);
+  const T* F = R;
+  if (c.gamma > 0.0) {
+    Tmp<T> mg(c.pool, Kp);
+    mass_inverse<T>(c, rg, mg, c.opt.mass_steps_al, K);
+    bt_apply_k<T>(c, K, mg, Fg, (const T*)nullptr, R, c.gamma * c.mu);
+    F = Fg;
+  }
+  zero<T>(c, X, Kv + Kp);
+  // systems left out get a zero right-hand side: their inner solves stop at once
+  Tmp<T> Fl(c.pool, Kv);
+  double keep[kMaxRhs] = {};
+  for (int k = 0; k < K; ++k) keep[k] = has_bit(live, k) ? 1.0 : 0.0;
+  kaxpby<T>(c.ex, nv, 0, K, 1, KCoefs::host(keep, K), F, KCoefs::constant(0.0), Fl);
+  ainv_k<T>(c, K, Fl, dU, tol_in);
+  Tmp<T> r(c.pool, Kp), z(c.pool, Kp), d(c.pool, Kp), q(c.pool, Kp), rold(c.pool, Kp);
+  Tmp<T> t(c.pool, Kv), wd(c.pool, Kv);
+  b_apply_k<T>(c, K, dU, r, rg, -1.0);  // r = rg - B w
+  project_mean_k<T>(c, r, np, K);
+  Scalars& S = c.sc;
+  const int s = S.take(6 * K);
+  struct Give {
+    Scalars& S;
+    int n;
+    ~Give() { S.give(n); }
+  } give{S, 6 * K};
+  double* D = S.d + s;  // [0,K), [2K,3K): z.r (alternating); [K,2K): d.q; [3K,4K): z.r_old; [4K,5K): r.r;
+                        // [5K,6K): beta numerators
+  kdot<T>(c.ex, c.ds, np, 0, K, 1, r, r, D + 4 * K);
+  read_k(c, D + 4 * K, s + 4 * K, K);
+  double rr0[kMaxRhs] = {};
+  unsigned act = live;
+  for (int k = 0; k < K; ++k) {
+    rr0[k] = S.h[s + 4 * K + k];
+    if (!std::isfinite(rr0[k])) throw Error(STOKES_ERR_NAN, "non-finite Schur right-hand side");
+    if (rr0[k] == 0.0) act &= ~(1u << k);
+  }
+  if (!act) return;
+  cprec_k<T>(c, K, r, z);
+  kaxpby<T>(c.ex, np, 0, K, 1, KCoefs::constant(1.0).mask(act), z, KCoefs::constant(0.0), d);
+  int irz = 0, irzn = 2;
+  kdot<T>(c.ex, c.ds, np, 0, K, 1, z, r, D + irz * K);
+  int it = 0;
+  while (it < c.opt.max_outer) {
+    bt_apply_k<T>(c, K, d, t, (const T*)nullptr, (const T*)nullptr, 1.0);  // t = B^T d
+    ainv_k<T>(c, K, t, wd, tol_in);                                         // wd = A^{-1} t
+    b_apply_k<T>(c, K, wd, q, (const T*)nullptr, 1.0);                      // q = S d
+    kdot<T>(c.ex, c.ds, np, 0, K, 1, d, q, D + K);
+    KCoefs alpha = KCoefs::ratio(D + irz * K, D + K).mask(act);
+    kaxpby<T>(c.ex, np, 0, K, 1, alpha, d, KCoefs::constant(1.0), dP);
+    kaxpby<T>(c.ex, nv, 0, K, 1, alpha, wd, KCoefs::constant(1.0), dU);
+    copy<T>(c, rold, r, Kp);
+    kaxpby<T>(c.ex, np, 0, K, 1, KCoefs::ratio(D + irz * K, D + K, -1.0).mask(act), q, KCoefs::constant(1.0), r);
+    project_mean_k<T>(c, r, np, K);
+    ++it;
+    for (int k = 0; k < K; ++k)
+      if (has_bit(act, k)) ++its[k];
+    kdot<T>(c.ex, c.ds, np, 0, K, 1, r, r, D + 4 * K);
+    read_k_issue(c, D + 4 * K, s + 4 * K, K);
+    cprec_k<T>(c, K, r, z);
+    SK_CUDA(cudaEventSynchronize(c.ev_read));
+    for (int k = 0; k < K; ++k) {
+      if (!has_bit(act, k)) continue;
+      const double rr = S.h[s + 4 * K + k];
+      if (!std::isfinite(rr)) throw Error(STOKES_ERR_NAN, "non-finite Schur residual");
+      if (std::sqrt(rr) <= eta[k] * std::sqrt(rr0[k])) act &= ~(1u << k);
+    }
+    if (!act) break;
+    kdot<T>(c.ex, c.ds, np, 0, K, 1, z, r, D + irzn * K);
+    kdot<T>(c.ex, c.ds, np, 0, K, 1, z, rold, D + 3 * K);
+    ksub(c.ex, K, D + 5 * K, D + irzn * K, D + 3 * K);  // Polak-Ribiere numerator
+    // d = z + beta d for the systems still iterating, 0 for the others
+    kaxpby<T>(c.ex, np, 0, K, 1, KCoefs::constant(1.0).mask(act), z, KCoefs::cg_ratio(D + 5 * K, D + irz * K).mask(act),
+              d);
+    std::swap(irz, irzn);
+  }
+  c.outer_iters += it;
+  if (act) c.outer_capped = true;
+}
+
 // Method 2 (right-preconditioned FGMRES(m), CGS2) for the K systems of the
 // residual K-vector R (rF blocks, then rg blocks) into the K-vector X, in
 // lockstep: one Arnoldi step of every live system per iteration, one host
@@ -1560,7 +1653,10 @@ static void correction_k(stokes_ctx& c, int K, const double* R, double* X, const
     convert<double, float>(c.ex, KN, R, R32);
     Rt = R32;
   }
-  method2_k<T>(c, K, Rt, dX, eta, tol_in, live, its);
+  if (c.opt.method == STOKES_METHOD_COUPLED)
+    method2_k<T>(c, K, Rt, dX, eta, tol_in, live, its);
+  else
+    method1_k<T>(c, K, Rt, dX, eta, tol_in, live, its);
   add_convert<T, double>(c.ex, KN, dX, X);
 }
 
@@ -1664,10 +1760,9 @@ static void solve_reduced_k(stokes_ctx& c, int K, const double* F, const double*
   }
 }
 
-// K forces f [K][(2n+1)^3][3] -> u [K][(2n+1)^3][3], p [K][(n+1)^3]. Method 2
-// solves groups of kLockstep systems in lockstep (a short last group is padded
-// with zero systems; a single one takes the one-system path); Method 1 solves
-// the systems one after another.
+// K forces f [K][(2n+1)^3][3] -> u [K][(2n+1)^3][3], p [K][(n+1)^3]: groups
+// of kLockstep systems in lockstep (a short last group is padded with zero
+// systems; a single one takes the one-system path).
 int solve_multi_context(stokes_ctx* cp, int K, const double* f, const double* g, double tol, double* u, double* p,
                         stokes_info* info) {
   stokes_ctx& c = *cp;
@@ -1681,7 +1776,7 @@ int solve_multi_context(stokes_ctx* cp, int K, const double* f, const double* g,
   };
   for (int k0 = 0; k0 < K;) {
     const int left = K - k0;
-    if (c.opt.method != STOKES_METHOD_COUPLED || left == 1) {
+    if (left == 1) {
       note(solve_context(cp, f + k0 * Nall, g ? g + k0 * np : nullptr, tol, u + k0 * Nall, p + k0 * np,
                          info ? info + k0 : nullptr));
       ++k0;

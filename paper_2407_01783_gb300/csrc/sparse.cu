@@ -658,8 +658,15 @@ __device__ __forceinline__ double4 ldcs_vec(const double4* p) {
 // points per axis). An x-neighbour outside the space may wrap into the
 // adjacent line, but its stored weight is exactly 0. So rows need no test
 // except near the y/z boundary, and no warp diverges at x-line ends.
+#ifndef SK_ST_BLOCK
+#define SK_ST_BLOCK 128  // threads per block of the stencil kernel
+#endif
+#ifndef SK_ST_UNROLL
+#define SK_ST_UNROLL 2   // 4-entry groups unrolled (their loads in flight together)
+#endif
+constexpr int kStUnroll = SK_ST_UNROLL;
 template <int NR, class TM, class T, class Epi>
-__global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __restrict__ v, const T* __restrict__ x,
+__global__ void __launch_bounds__(SK_ST_BLOCK) k_stencil(const StArgs a, const TM* __restrict__ v, const T* __restrict__ x,
                                                  size_t xs, Epi epi) {
   int c, r;
   if (!st_locate(a, c, r)) return;
@@ -680,7 +687,7 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
   // outside the vector, so it is clamped into [0, xs): every row takes the same
   // branch-free loop and the zero weight cancels the clamped read.
   const int last = (int)xs - 1;
-#pragma unroll 2
+#pragma unroll kStUnroll
   for (int e4 = 0; e4 < S4; ++e4) {
     const V4 w4 = ldcs_vec(&vr[e4 * rc]);  // streamed once: evict first
     const TM wv[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -707,7 +714,7 @@ __global__ void __launch_bounds__(128) k_stencil(const StArgs a, const TM* __res
 
 template <class T, class Epi>
 static void launch_stencil(const Exec& ex, const StencilOp& so, int nr, const T* x, const Epi& epi) {
-  const int bs = 128;
+  const int bs = SK_ST_BLOCK;
   StArgs a = stencil_args(so, bs, kStencilRows);
   int grid = a.bbeg[so.ncls];
   if (grid == 0) return;

@@ -1,7 +1,8 @@
-"""Several right-hand sides in one call (stokes_solve_multi): Method 2 solves
-four systems in lockstep, sharing every V-cycle, mass-inverse and vector-kernel
-sweep. Each system is checked on its own against the oracle's exact discrete
-solution and the oracle's residual of the GPU answer."""
+"""Several right-hand sides in one call (stokes_solve_multi): four systems in
+lockstep (Method 2 FGMRES or Method 1 Schur CG), sharing every V-cycle,
+mass-inverse, product and vector-kernel sweep. Each system is checked on its
+own against the oracle's exact discrete solution and the oracle's residual of
+the GPU answer."""
 
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ from gpu_helpers import cuda, gpu_module, host, rel_err
 pytestmark = pytest.mark.gpu
 
 
-def multi_case(n, mu, dt, k, tol, seed=11, gamma=0.0, pressure_load=False, zero=(), scale=None, **opt):
+def multi_case(n, mu, dt, k, tol, seed=11, gamma=0.0, pressure_load=False, zero=(), scale=None, method=1, **opt):
     sk = gpu_module()
     V = wl.kuhn_vertices(n, 0.2, seed)
     orc = StokesSystem(KuhnMesh(n, V), mu, dt)
@@ -27,7 +28,7 @@ def multi_case(n, mu, dt, k, tol, seed=11, gamma=0.0, pressure_load=False, zero=
         for j, a in scale.items():
             fs[j] = a * fs[j]
     gs = [wl.random_pressure_load(n, 200 * seed + j) for j in range(k)] if pressure_load else None
-    S = sk.Stokes(n, V, mu, dt, gamma, sk.stokes_default_options(method=sk.METHOD_COUPLED, **opt))
+    S = sk.Stokes(n, V, mu, dt, gamma, sk.stokes_default_options(method=method, **opt))
     F = cuda(np.stack(fs))
     G = cuda(np.stack(gs)) if gs is not None else None
     U, P, infos = S.solve_multi(F, G, tol)
@@ -114,3 +115,26 @@ def test_inner_cg_velocity_solves():
     for r in res:
         assert r["info"]["status"] == 0 and r["info"]["rel_residual"] <= 1e-11
         assert r["eu"] <= 1e-8 and r["ep"] <= 1e-8, (r["eu"], r["ep"])
+
+
+@pytest.mark.parametrize("gamma", [0.0, 1.0])
+def test_schur_cg_lockstep_fp64_matches_oracle(gamma):
+    """Method 1 (flexible Schur CG, lockstep inner PCG with per-system
+    stopping) in FP64 to 1e-12 with pressure loads: each system within the
+    1e-9 parity bar."""
+    res = multi_case(6, 1e-2, 1e-3, 4, 1e-12, seed=17, gamma=gamma, pressure_load=True, method=0)
+    for r in res:
+        assert r["info"]["status"] == 0 and r["info"]["rel_residual"] <= 1e-12, r["info"]
+        assert r["eu"] <= 1e-9 and r["ep"] <= 1e-9, (r["eu"], r["ep"])
+        assert abs(r["mean"]) < 1e-12
+
+
+def test_schur_cg_lockstep_mixed_with_zero_system():
+    """Method 1, mixed precision to 1e-8, one zero force among four."""
+    res = multi_case(8, 1e-3, 1e-3, 4, 1e-8, seed=18, zero=(2,), method=0, precision=1, vcycles=1)
+    assert np.all(res[2]["U"] == 0) and np.all(res[2]["P"] == 0)
+    for j in (0, 1, 3):
+        r = res[j]
+        assert r["info"]["status"] == 0 and r["info"]["rel_residual"] <= 1e-8, r["info"]
+        assert r["res"] <= 1e-8 * (1 + 1e-6), r["res"]
+        assert r["eu"] < 1e-5 and r["ep"] < 1e-4, (r["eu"], r["ep"])
