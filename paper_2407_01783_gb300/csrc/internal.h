@@ -184,6 +184,18 @@ __device__ __forceinline__ void df_madd(DF& s, float ah, float al, float xh, flo
   s.h = t;
   s.l = __fadd_rn(s.l, __fadd_rn(e, __fadd_rn(pe, pc)));
 }
+// s += a * b with both rounding errors kept (the Dot2 step of Ogita, Rump &
+// Oishi 2005: TwoProduct by FMA, then TwoSum): a dot product of FP32 vectors
+// as accurate as if accumulated in twice the working precision, on FP32 units
+__device__ __forceinline__ void df_dot(DF& s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s.h, p);
+  const float z = __fsub_rn(t, s.h);
+  const float e = __fadd_rn(__fsub_rn(s.h, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s.h = t;
+  s.l = __fadd_rn(s.l, __fadd_rn(e, pe));
+}
 __device__ __forceinline__ void df_add(DF& s, float oh, float ol) {
   const float t = __fadd_rn(s.h, oh);
   const float z = __fsub_rn(t, s.h);
@@ -547,6 +559,8 @@ template <class T> void sym3_launch4(const Exec& ex, const Csr& m, const T* x, T
 template <class T> void bsr3_apply_k(const Exec& ex, const Csr& m, int k, const T* x, T* y, const T* b,
                                      int kind = STOKES_KERNEL_SPMV_A);
 void sym3_residual_df(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y);
+// the same for four right-hand sides [4][3][rows] in one sweep
+void sym3_residual_df4(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y);
 double sym3_bytes(const Sym3Op& so, int esz, int rows, int streams);
 // most blocks of one symmetric-stencil product launch (fused-dot partial capacity)
 int sym3_grid(const Sym3Op& so);

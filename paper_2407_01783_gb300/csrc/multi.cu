@@ -6,9 +6,11 @@
 // by the pressures [K][np]. The "segment" of right-hand side k is its
 // velocity part, its pressure part, or both. Every kernel here runs a 2D grid:
 // blockIdx.y is the right-hand side, so the K systems keep their own
-// coefficients and dot products while sharing one launch. Dot products
-// accumulate in FP64 and are reduced in a fixed order (grid_sum per k).
+// coefficients and dot products while sharing one launch. Dot products are
+// reduced in a fixed order (deterministic): per-thread sums in FP64 (FP64
+// vectors) or double-float (FP32 vectors), FP64 across threads.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -29,15 +31,27 @@ struct KSeg {
   }
 };
 
+// Per-thread sums: FP64 for FP64 vectors; for FP32 vectors double-float
+// (df_dot) on the FP32 units, since FP64 arithmetic is scarce on this GPU and
+// would bound these kernels before memory does. Across threads: FP64.
 template <class T>
 __global__ void __launch_bounds__(256) k_kdot(KSeg s, const T* __restrict__ x, const T* __restrict__ y,
                                               double* partial, unsigned* counter, double* out) {
   const int k = blockIdx.y;
   const size_t n = s.len();
   double t = 0.0;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = s.at(k, e);
-    t += (double)x[i] * (y ? (double)y[i] : 1.0);
+  if constexpr (std::is_same<T, float>::value) {
+    DF a{0.f, 0.f};
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+      const size_t i = s.at(k, e);
+      df_dot(a, x[i], y ? y[i] : 1.f);
+    }
+    t = (double)a.h + (double)a.l;
+  } else {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+      const size_t i = s.at(k, e);
+      t += (double)x[i] * (y ? (double)y[i] : 1.0);
+    }
   }
   grid_sum(t, partial + (size_t)k * gridDim.x, counter + k, out + k);
 }
@@ -81,14 +95,29 @@ __global__ void __launch_bounds__(256) k_kmdot(KSeg s, KBasis<T> V, int J, const
   const int k = blockIdx.y;
   const size_t n = s.len();
   double acc[KB];
+  if constexpr (std::is_same<T, float>::value) {  // double-float per thread, as k_kdot
+    DF a[KB];
 #pragma unroll
-  for (int i = 0; i < KB; ++i) acc[i] = 0.0;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t a = s.at(k, e);
-    const double we = (double)w[a];
+    for (int i = 0; i < KB; ++i) a[i] = DF{0.f, 0.f};
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+      const size_t q = s.at(k, e);
+      const float we = w[q];
 #pragma unroll
-    for (int i = 0; i < KB; ++i)
-      if (i < J) acc[i] += (double)V.v[i][a] * we;
+      for (int i = 0; i < KB; ++i)
+        if (i < J) df_dot(a[i], V.v[i][q], we);
+    }
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = (double)a[i].h + (double)a[i].l;
+  } else {
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+      const size_t a = s.at(k, e);
+      const double we = (double)w[a];
+#pragma unroll
+      for (int i = 0; i < KB; ++i)
+        if (i < J) acc[i] += (double)V.v[i][a] * we;
+    }
   }
   __shared__ double sh[8][KB];
   __shared__ bool last;

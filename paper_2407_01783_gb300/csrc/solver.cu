@@ -77,6 +77,7 @@ template <class T> static void project_mean(stokes_ctx& c, T* r, size_t n, int m
 }
 
 static size_t nvel(const stokes_ctx& c) { return 3 * (size_t)c.lv[0].nvi; }
+static double nvi_of(const stokes_ctx& c) { return (double)c.lv[0].nvi; }
 static size_t npres(const stokes_ctx& c) { return (size_t)c.lv[0].np; }
 
 // ---------------------------------------------------------------------------
@@ -1620,7 +1621,18 @@ static void method2_k(stokes_ctx& c, int K, const T* R, T* X, const double* eta,
 static void full_residual_k(stokes_ctx& c, int K, const double* F, const double* g, const double* X, double* R,
                             const double* normFg, double* rel) {
   const size_t nv = nvel(c), np = npres(c), Kv = (size_t)K * nv;
-  for (int k = 0; k < K; ++k) {
+  if (K == 4 && c.A.v32lo && c.A.sym && c.A.sym->v32lo) {  // one sweep of each matrix for the four
+    Tmp<float> uh(c.pool, Kv), ul(c.pool, Kv);
+    split_f64(c.ex, Kv, X, uh, ul);
+    {
+      // values hi + lo once; per right-hand side x hi + lo, b and y (FP64)
+      ProfScope ps(c.ex, STOKES_KERNEL_RESIDUAL, 8.0 * (double)c.A.sym->total + 4.0 * 3.0 * nvi_of(c) * 24.0);
+      sym3_residual_df4(c.ex, c.A, uh, ul, F, R);
+    }
+    bt_apply<double>(c.ex, c.Bt, X + Kv, R, (const double*)nullptr, R, 1.0, 4);
+    b_apply<double>(c.ex, c.B, X, R + Kv, g, -1.0, 4);
+  } else {
+   for (int k = 0; k < K; ++k) {
     const double* Uk = X + k * nv;
     double* rFk = R + k * nv;
     if (c.A.v32lo) {
@@ -1632,6 +1644,7 @@ static void full_residual_k(stokes_ctx& c, int K, const double* F, const double*
     }
     bt_apply<double>(c.ex, c.Bt, X + Kv + k * np, rFk, (const double*)nullptr, rFk, 1.0);
     b_apply<double>(c.ex, c.B, Uk, R + Kv + k * np, g + k * np, -1.0);
+   }
   }
   const int s = c.sc.take(K);
   kdot<double>(c.ex, c.ds, nv, np, K, 3, R, R, c.sc.d + s);

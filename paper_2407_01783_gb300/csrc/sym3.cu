@@ -228,8 +228,10 @@ __global__ void __launch_bounds__(kSymBlock) k_sym3(const Sym3Args a, int nvb, c
   if (DOT) grid_sum(part, partial, counter, dot);
 }
 
-// y = b - A x in double-float arithmetic: A = vh + vl, x = xh + xl (FP32 pairs)
-template <int G>
+// y = b - A x in double-float arithmetic: A = vh + vl, x = xh + xl (FP32
+// pairs); K right-hand sides (x, b, y: 3K component-major components), each
+// stored block read once for all K
+template <int G, int K = 1>
 __global__ void __launch_bounds__(kSymBlock) k_sym3_df(const Sym3Args a, const float* __restrict__ vh,
                                                       const float* __restrict__ vl, const float* __restrict__ xh,
                                                       const float* __restrict__ xl, size_t xs,
@@ -238,8 +240,10 @@ __global__ void __launch_bounds__(kSymBlock) k_sym3_df(const Sym3Args a, const f
   const int lane = (int)threadIdx.x % G;
   const int c = R.c;
   const int last = (int)xs - 1;
-  DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  constexpr int U = SymBatch<G>::U > 4 ? 4 : SymBatch<G>::U;
+  DF acc[3 * K];
+#pragma unroll
+  for (int r = 0; r < 3 * K; ++r) acc[r] = DF{0.f, 0.f};
+  constexpr int U = K > 1 ? 1 : (SymBatch<G>::U > 4 ? 4 : SymBatch<G>::U);
   if (R.valid) {
     const size_t rc = (size_t)a.prows[c];
     const int u0 = a.ubeg[c], nu = a.ubeg[c + 1] - u0;
@@ -261,15 +265,18 @@ __global__ void __launch_bounds__(kSymBlock) k_sym3_df(const Sym3Args a, const f
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        float x_h[3], x_l[3];
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) x_h[q] = xh[q * xs + cc[u]], x_l[q] = xl[q * xs + cc[u]];
+        for (int k = 0; k < K; ++k) {
+          float x_h[3], x_l[3];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+          for (int q = 0; q < 3; ++q) x_h[q] = xh[(3 * k + q) * xs + cc[u]], x_l[q] = xl[(3 * k + q) * xs + cc[u]];
 #pragma unroll
-          for (int q = 0; q < 3; ++q) df_madd(acc[r], wh[u][3 * r + q], wl[u][3 * r + q], x_h[q], x_l[q]);
-      }
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              df_madd(acc[3 * k + r], wh[u][3 * r + q], wl[u][3 * r + q], x_h[q], x_l[q]);
+        }
     }
     const int l0 = a.lbeg[c], nl = a.lbeg[c + 1] - l0;
     for (int e0 = lane; e0 < nl; e0 += U * G) {
@@ -294,29 +301,31 @@ __global__ void __launch_bounds__(kSymBlock) k_sym3_df(const Sym3Args a, const f
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        float x_h[3], x_l[3];
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) x_h[q] = xh[q * xs + cc[u]], x_l[q] = xl[q * xs + cc[u]];
+        for (int k = 0; k < K; ++k) {
+          float x_h[3], x_l[3];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+          for (int q = 0; q < 3; ++q) x_h[q] = xh[(3 * k + q) * xs + cc[u]], x_l[q] = xl[(3 * k + q) * xs + cc[u]];
 #pragma unroll
-          for (int q = 0; q < 3; ++q)  // transpose of A(j, i)
-            df_madd(acc[r], wh[u][3 * q + r], wl[u][3 * q + r], x_h[q], x_l[q]);
-      }
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)  // transpose of A(j, i)
+              df_madd(acc[3 * k + r], wh[u][3 * q + r], wl[u][3 * q + r], x_h[q], x_l[q]);
+        }
     }
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1)
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 3 * K; ++r) {
       const float oh = __shfl_xor_sync(0xffffffffu, acc[r].h, o);
       const float ol = __shfl_xor_sync(0xffffffffu, acc[r].l, o);
       df_add(acc[r], oh, ol);
     }
   if (R.valid && lane == 0) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 3 * K; ++r) {
       const size_t i = r * xs + R.row;
       y[i] = b[i] - ((double)acc[r].h + (double)acc[r].l);
     }
@@ -401,6 +410,16 @@ static void sym3_df_g(const Exec& ex, const Csr& m, const float* xh, const float
   const int grid = sym3_blocks(so, a);
   if (grid == 0) return;
   k_sym3_df<G><<<grid, kSymBlock, 0, ex.s>>>(a, so.v32, so.v32lo, xh, xl, (size_t)m.rows, b, y);
+  SK_CHECK_LAUNCH();
+}
+
+// four right-hand sides in one sweep (one thread per row, one entry in flight)
+void sym3_residual_df4(const Exec& ex, const Csr& m, const float* xh, const float* xl, const double* b, double* y) {
+  const Sym3Op& so = *m.sym;
+  const Sym3Args a = sym3_args(so, 1);
+  const int grid = sym3_blocks(so, a);
+  if (grid == 0) return;
+  k_sym3_df<1, 4><<<grid, kSymBlock, 0, ex.s>>>(a, so.v32, so.v32lo, xh, xl, (size_t)m.rows, b, y);
   SK_CHECK_LAUNCH();
 }
 

@@ -42,7 +42,8 @@ def test_benchmark_batch_every_solution_checked_by_oracle():
     """The benchmark's uneven batch exactly as bench.py runs it: 32 seeded
     instances (n in 12..40, mu log-U[1e-4, 1], dt log-U[1e-4, 1e-2]), 4 N(0,1)
     body forces each, coupled FGMRES(30) + block-LU, mixed precision, one
-    V-cycle, one context and stream per instance, solved concurrently to 1e-8.
+    V-cycle, one context and stream per instance, the four forces of an
+    instance in lockstep (stokes_solve_multi), solved concurrently to 1e-8.
     Every row of every one of the 128 residuals is evaluated by the oracle's
     element loop; the smallest instance (n = 12) is also compared with the
     oracle's exact discrete solution."""

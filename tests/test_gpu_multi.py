@@ -138,3 +138,15 @@ def test_schur_cg_lockstep_mixed_with_zero_system():
         assert r["info"]["status"] == 0 and r["info"]["rel_residual"] <= 1e-8, r["info"]
         assert r["res"] <= 1e-8 * (1 + 1e-6), r["res"]
         assert r["eu"] < 1e-5 and r["ep"] < 1e-4, (r["eu"], r["ep"])
+
+
+@pytest.mark.parametrize("opt", [dict(format=1), dict(format=2), dict(vel_prec=1), dict(schur_prec=1),
+                                 dict(schur_prec=2), dict(method=0, format=3)])
+def test_lockstep_option_variants(opt):
+    """The lockstep path under the storage formats (CSR/BSR3 only, stencils
+    everywhere, BSR3 products), the block velocity V-cycle (one right-hand
+    side per cycle), C^Delta and C_lambda with the velocity mass."""
+    res = multi_case(5, 1e-2, 1e-3, 4, 1e-11, seed=19, **opt)
+    for r in res:
+        assert r["info"]["status"] == 0 and r["info"]["rel_residual"] <= 1e-11, r["info"]
+        assert r["eu"] <= 1e-8 and r["ep"] <= 1e-8, (r["eu"], r["ep"])
