@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -193,13 +194,29 @@ template <class T> struct MultiArgs {
 template <class T, int K>
 __global__ void __launch_bounds__(256) k_mdot(MultiArgs<T> a) {
   double s[K];
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 vectors: per-thread double-float sums (df_dot) on the FP32 units
+    // (FP64 arithmetic would bound the kernel before memory does)
+    DF d[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) s[i] = 0.0;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.n; e += (size_t)gridDim.x * blockDim.x) {
-    const double we = (double)a.wr[e];
+    for (int i = 0; i < K; ++i) d[i] = DF{0.f, 0.f};
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.n; e += (size_t)gridDim.x * blockDim.x) {
+      const float we = a.wr[e];
 #pragma unroll
-    for (int i = 0; i < K; ++i)
-      if (i < a.k) s[i] += (double)a.v[i][e] * we;
+      for (int i = 0; i < K; ++i)
+        if (i < a.k) df_dot(d[i], a.v[i][e], we);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) s[i] = (double)d[i].h + (double)d[i].l;
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) s[i] = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.n; e += (size_t)gridDim.x * blockDim.x) {
+      const double we = (double)a.wr[e];
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i < a.k) s[i] += (double)a.v[i][e] * we;
+    }
   }
   __shared__ double sh[8][K];
   __shared__ bool last;
