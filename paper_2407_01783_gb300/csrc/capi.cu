@@ -346,17 +346,18 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   }
   clock.mark(STOKES_SETUP_COPIES);
   // threads-per-row: tuned in the precision of the hot loop unless fixed by the caller
-  auto tune = [&](Csr& m, int nr, int kind) {
+  auto tune = [&](Csr& m, int nr, int kind, int k = 1) {
     if (c.opt.spmv_group > 0) {
       int g = 1;
       while (g < c.opt.spmv_group && g < 32) g <<= 1;
-      m.group = g;
+      (k > 1 ? m.group4 : m.group) = g;
       return;
     }
     Csr probe = m;
     if (c.mixed && m.v32) probe.v64 = nullptr;
-    autotune_group(c.ex, probe, nr, kind);
+    autotune_group(c.ex, probe, nr, kind, k);
     m.group = probe.group;
+    m.group4 = probe.group4;
   };
   tune(c.A, 3, 1);
   // threads per row of the symmetric A products: one (measured fastest inside
@@ -367,6 +368,8 @@ void setup_context(stokes_ctx* cp, int n, const double* Xh) {
   }
   tune(c.B, 1, 2);
   tune(c.Bt, 3, 3);
+  tune(c.B, 1, 2, 4);  // four right-hand sides (stokes_solve_multi)
+  tune(c.Bt, 3, 3, 4);
   tune(c.MQ, 1, 0);
   if (c.MV.v64) tune(c.MV, 3, 0);
   c.LQ.group = c.MQ.group;

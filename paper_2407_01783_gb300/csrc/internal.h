@@ -256,6 +256,7 @@ struct Csr {
   float* v32 = nullptr;
   float* v32lo = nullptr;  // v64 - v32 rounded to FP32 (double-float residual), or null
   int group = 8;  // threads per row
+  int group4 = 0; // threads per row of four-right-hand-side products (B, B^T; 0: group)
   const StencilOp* st = nullptr;  // same matrix in stencil storage (used when set, see st_min_single)
   int st_min_single = 0;          // component-major products (one right-hand side) use the stencil
                                   // storage only on matrices with at least this many rows
@@ -462,6 +463,11 @@ template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* 
 // Chebyshev step: r = b - A xin; d = c1 d + c2 dinv r; xout = xin + d.
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin,
                                   T* d, T* xout, const T* dinv, double c1, double c2, int kind, bool il = false);
+// the first two Chebyshev steps from x = 0 in one sweep (node-interleaved,
+// nr = 4 or 12): x1 = d1 = s0 D^-1 b formed at each gathered column, then
+// d = c1 d1 + c2 D^-1 (b - A x1), xout = x1 + d
+template <class T> void spmv_cheb_first_il(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
+                                           const T* dinv, double s0, double c1, double c2, int kind);
 // BSR3 strain-form A: y = A x or y = b - A x (b may be null).
 template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b,
                                    int kind = STOKES_KERNEL_SPMV_A);
@@ -484,7 +490,8 @@ template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, cons
 template <class T> void dense_apply(const Exec& ex, const T* Minv, int m, int nr, const T* b, T* y,
                                     bool il = false);
 
-void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3);
+// threads per row (m.group, or m.group4 for k = 4 right-hand sides of B / B^T)
+void autotune_group(const Exec& ex, Csr& m, int nr, int kind_bsr3, int k = 1);
 
 
 // ---------------------------------------------------------------------------

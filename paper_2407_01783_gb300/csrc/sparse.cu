@@ -273,6 +273,39 @@ template <class T, int NR> struct EpiChebIL {
   }
 };
 
+// First two Chebyshev steps from x = 0 in one sweep (node-interleaved): the
+// kernel gathers b, and every gathered value is scaled by s0 D^-1 at its
+// column, which is the first iterate x1 = d1 = s0 D^-1 b; the epilogue then
+// takes the second step r = b - A x1, d = c1 d1 + c2 D^-1 r, x2 = x1 + d.
+template <class T, int NR> struct EpiChebFirstIL {
+  static constexpr int nr = NR;
+  static constexpr bool il = true;
+  static constexpr bool first = true;
+  const T* b;
+  T* d;
+  T* xout;
+  const T* dinv;
+  T s0, c1, c2;
+  __device__ __forceinline__ T gather_scale(size_t col) const { return s0 * dinv[col]; }
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    const T di = dinv[row];
+    const size_t o = (size_t)row * NR;
+    T bv[NR], dv[NR];
+    ldv<T, NR>(b + o, bv);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T x1 = s0 * di * bv[r];
+      const T dn = c1 * x1 + c2 * di * (bv[r] - acc[r]);
+      dv[r] = dn;
+      bv[r] = x1 + dn;
+    }
+    stv<T, NR>(d + o, dv);
+    stv<T, NR>(xout + o, bv);
+  }
+};
+template <class E, class = void> struct is_first : std::false_type {};
+template <class E> struct is_first<E, std::void_t<decltype(E::first)>> : std::integral_constant<bool, E::first> {};
+
 template <int G, class T, int NR>
 __device__ __forceinline__ void group_reduce(T* acc) {
 #pragma unroll
@@ -321,6 +354,14 @@ __global__ void __launch_bounds__(256) k_csr(int rows, const int* __restrict__ r
       if constexpr (Epi::il) {
 #pragma unroll
         for (int u = 0; u < U; ++u) ldv<T, NR>(x + (size_t)c[u] * NR, xv[u]);
+        if constexpr (is_first<Epi>::value) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const T f = epi.gather_scale(c[u]);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) xv[u][r] *= f;
+          }
+        }
       } else {
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -699,8 +740,10 @@ __global__ void __launch_bounds__(SK_ST_BLOCK) k_stencil(const StArgs a, const T
       for (int j = 0; j < 4; ++j) {
         T xv[NR];
         ldv<T, NR>(x + cc[j] * NR, xv);
+        T w = (T)wv[j];
+        if constexpr (is_first<Epi>::value) w *= epi.gather_scale(cc[j]);
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * xv[q];
+        for (int q = 0; q < NR; ++q) acc[q] += w * xv[q];
       }
     } else {
 #pragma unroll
@@ -861,6 +904,20 @@ template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T*
     run_scalar(ex, m, st, xin, EpiCheb<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
   });
 }
+template <class T> void spmv_cheb_first_il(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
+                                           const T* dinv, double s0, double c1, double c2, int kind) {
+  require_il(nr, true);
+  const bool st = use_stencil<T>(m, true);
+  // streams: b gathered, d and x_out written, D^-1 gathered
+  ProfScope ps(ex, kind,
+               (st ? stencil_bytes(*m.st, sizeof(T), nr, 2) : prod_bytes(m, sizeof(T), nr, nr, 2)) +
+                   (double)sizeof(T) * m.rows);
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    if constexpr (il_ok<NR>())
+      run_scalar(ex, m, st, b, EpiChebFirstIL<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2});
+  });
+}
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
                                   const T* dinv, double c1, double c2, int kind) {
   // streams as in the scalar step, over 3 components and a 3-component diagonal
@@ -917,7 +974,7 @@ template <class T> bool bsr3_apply_dot(const Exec& ex, const Csr& m, const T* x,
 template <class T> void b_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b, double alpha, int k) {
   SK_REQUIRE(k == 1 || k == 4, STOKES_ERR_ARG, "B product: 1 or 4 right-hand sides");
   ProfScope ps(ex, STOKES_KERNEL_B, m.bytes(sizeof(T)) + sizeof(T) * k * (3.0 * m.cols + m.rows * (b ? 2.0 : 1.0)));
-  if (k == 4) launch(ex, m, SH_B, x, EpiAxpy<T, 4>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group);
+  if (k == 4) launch(ex, m, SH_B, x, EpiAxpy<T, 4>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group4 ? m.group4 : m.group);
   else launch(ex, m, SH_B, x, EpiAxpy<T, 1>{b, nullptr, y, (T)alpha, (size_t)m.rows}, m.group);
 }
 template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* scale, const T* b,
@@ -926,7 +983,7 @@ template <class T> void bt_apply(const Exec& ex, const Csr& m, const T* x, T* y,
   ProfScope ps(ex, STOKES_KERNEL_BT,
                m.bytes(sizeof(T)) +
                    sizeof(T) * (k * (1.0 * m.cols + 3.0 * m.rows * (b ? 2.0 : 1.0)) + (scale ? m.rows : 0)));
-  if (k == 4) launch(ex, m, SH_BT, x, EpiAxpy<T, 12>{b, scale, y, (T)alpha, (size_t)m.rows}, m.group);
+  if (k == 4) launch(ex, m, SH_BT, x, EpiAxpy<T, 12>{b, scale, y, (T)alpha, (size_t)m.rows}, m.group4 ? m.group4 : m.group);
   else launch(ex, m, SH_BT, x, EpiAxpy<T, 3>{b, scale, y, (T)alpha, (size_t)m.rows}, m.group);
 }
 
@@ -1013,11 +1070,14 @@ static void tune_store(const std::string& key, int g) {
   std::fclose(fh);
 }
 
-void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
+void autotune_group(const Exec& ex, Csr& m, int nr, int kind, int k) {
   if (m.rows == 0) return;
   Shape sh = kind == 1 ? SH_BSR3 : kind == 2 ? SH_B : kind == 3 ? SH_BT : SH_CSR;
-  int xin = (sh == SH_BSR3 || sh == SH_B) ? 3 : (sh == SH_BT ? 1 : nr);
-  int yout = (sh == SH_BSR3 || sh == SH_BT) ? 3 : (sh == SH_B ? 1 : nr);
+  SK_REQUIRE(k == 1 || ((sh == SH_B || sh == SH_BT) && k == 4), STOKES_ERR_ARG,
+             "autotuner: four right-hand sides for B and B^T only");
+  int xin = k * ((sh == SH_BSR3 || sh == SH_B) ? 3 : (sh == SH_BT ? 1 : nr));
+  int yout = k * ((sh == SH_BSR3 || sh == SH_BT) ? 3 : (sh == SH_B ? 1 : nr));
+  int& slot = k > 1 ? m.group4 : m.group;
   bool f32 = m.v64 == nullptr;
   size_t esz = f32 ? 4 : 8;
   int dev = 0;
@@ -1028,14 +1088,14 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   for (char& ch : devname)
     if (ch == ' ') ch = '_';
   char key[512];
-  std::snprintf(key, sizeof(key), "v%d|%s|sh%d|f%d|r%d|c%d|z%lld", kTuneVersion, devname.c_str(), (int)sh,
-                f32 ? 32 : 64, m.rows, m.cols, (long long)m.nnz);
+  std::snprintf(key, sizeof(key), "v%d|%s|sh%d|f%d|r%d|c%d|z%lld%s", kTuneVersion, devname.c_str(), (int)sh,
+                f32 ? 32 : 64, m.rows, m.cols, (long long)m.nnz, k > 1 ? "|k4" : "");
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_load();
     auto it = g_tune->find(key);
     if (it != g_tune->end()) {
-      m.group = it->second;
+      slot = it->second;
       return;
     }
   }
@@ -1048,18 +1108,16 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   SK_CUDA(cudaEventCreate(&e1));
   Exec plain{ex.s, nullptr};
   float best = FLT_MAX;
-  int bestg = m.group;
+  int bestg = slot ? slot : m.group;
   const int gs[5] = {2, 4, 8, 16, 32};
   for (int gi = 0; gi < 5; ++gi) {
     int g = gs[gi];
     auto run = [&]() {
-      if (f32) {
-        if (yout == 3) launch(plain, m, sh, (const float*)x, EpiStore<float, 3>{(float*)y, (size_t)m.rows}, g);
-        else launch(plain, m, sh, (const float*)x, EpiStore<float, 1>{(float*)y, (size_t)m.rows}, g);
-      } else {
-        if (yout == 3) launch(plain, m, sh, (const double*)x, EpiStore<double, 3>{(double*)y, (size_t)m.rows}, g);
-        else launch(plain, m, sh, (const double*)x, EpiStore<double, 1>{(double*)y, (size_t)m.rows}, g);
-      }
+      with_nr(yout, [&](auto NRc) {
+        constexpr int NR = decltype(NRc)::value;
+        if (f32) launch(plain, m, sh, (const float*)x, EpiStore<float, NR>{(float*)y, (size_t)m.rows}, g);
+        else launch(plain, m, sh, (const double*)x, EpiStore<double, NR>{(double*)y, (size_t)m.rows}, g);
+      });
     };
     run();
     float gbest = FLT_MAX;
@@ -1074,7 +1132,7 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
     }
     if (gbest < best) best = gbest, bestg = g;
   }
-  m.group = bestg;
+  slot = bestg;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(x);
@@ -1088,7 +1146,9 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind) {
   template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int, bool);                            \
   template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int, bool);                \
   template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
-                             double, int, bool);                                                                     \
+                             double, int, bool);                                                         \
+  template void spmv_cheb_first_il<T>(const Exec&, const Csr&, int, const T*, T*, T*, const T*, double,   \
+                                      double, double, int);                                                                     \
   template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, int);                          \
   template void bsr3_cheb<T>(const Exec&, const Csr&, const T*, const T*, T*, T*, const T*, double, double, int); \
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double, int);                \
