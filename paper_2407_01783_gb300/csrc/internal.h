@@ -463,11 +463,11 @@ template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* 
 // Chebyshev step: r = b - A xin; d = c1 d + c2 dinv r; xout = xin + d.
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin,
                                   T* d, T* xout, const T* dinv, double c1, double c2, int kind, bool il = false);
-// the first two Chebyshev steps from x = 0 in one sweep (node-interleaved,
-// nr = 4 or 12): x1 = d1 = s0 D^-1 b formed at each gathered column, then
-// d = c1 d1 + c2 D^-1 (b - A x1), xout = x1 + d
-template <class T> void spmv_cheb_first_il(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
-                                           const T* dinv, double s0, double c1, double c2, int kind);
+// the first two Chebyshev steps from x = 0 in one sweep: x1 = d1 = s0 D^-1 b
+// formed at each gathered column, then d = c1 d1 + c2 D^-1 (b - A x1),
+// xout = x1 + d (il: node-interleaved vectors, nr = 4 or 12)
+template <class T> void spmv_cheb_first(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
+                                        const T* dinv, double s0, double c1, double c2, int kind, bool il = false);
 // BSR3 strain-form A: y = A x or y = b - A x (b may be null).
 template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b,
                                    int kind = STOKES_KERNEL_SPMV_A);

@@ -101,12 +101,12 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
     if (block) bsr3_cheb<T>(c.ex, M, b, xin, d, xout, dinv, c1, c2, kind);
     else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind, il);
   };
-  if (xzero && il && !block && steps >= 2) {
+  if (xzero && !block && steps >= 2) {
     // the first two steps in one sweep; the output buffer is picked so that
     // the remaining steps' ping-pong ends in x
     const double rn = 1.0 / (2.0 * sigma - rho);
     T* out = (steps - 2) % 2 == 0 ? x : (T*)xt;
-    spmv_cheb_first_il<T>(c.ex, M, nr, b, d, out, dinv, 1.0 / theta, rn * rho, 2.0 * rn / delta, kind);
+    spmv_cheb_first<T>(c.ex, M, nr, b, d, out, dinv, 1.0 / theta, rn * rho, 2.0 * rn / delta, kind, il);
     rho = rn;
     xa = out;
     xb = out == x ? (T*)xt : x;

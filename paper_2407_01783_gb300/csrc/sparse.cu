@@ -303,6 +303,31 @@ template <class T, int NR> struct EpiChebFirstIL {
     stv<T, NR>(xout + o, bv);
   }
 };
+// the same on component-major vectors
+template <class T, int NR> struct EpiChebFirst {
+  static constexpr int nr = NR;
+  static constexpr bool il = false;
+  static constexpr bool first = true;
+  const T* b;
+  T* d;
+  T* xout;
+  const T* dinv;
+  T s0, c1, c2;
+  size_t ns;
+  __device__ __forceinline__ T gather_scale(size_t col) const { return s0 * dinv[col]; }
+  __device__ __forceinline__ void operator()(int row, const T* acc) const {
+    const T di = dinv[row];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const size_t i = r * ns + row;
+      const T bv = b[i];
+      const T x1 = s0 * di * bv;
+      const T dn = c1 * x1 + c2 * di * (bv - acc[r]);
+      d[i] = dn;
+      xout[i] = x1 + dn;
+    }
+  }
+};
 template <class E, class = void> struct is_first : std::false_type {};
 template <class E> struct is_first<E, std::void_t<decltype(E::first)>> : std::integral_constant<bool, E::first> {};
 
@@ -367,6 +392,14 @@ __global__ void __launch_bounds__(256) k_csr(int rows, const int* __restrict__ r
         for (int u = 0; u < U; ++u)
 #pragma unroll
           for (int r = 0; r < NR; ++r) xv[u][r] = x[r * xs + c[u]];
+        if constexpr (is_first<Epi>::value) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const T f = epi.gather_scale(c[u]);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) xv[u][r] *= f;
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -740,16 +773,28 @@ __global__ void __launch_bounds__(SK_ST_BLOCK) k_stencil(const StArgs a, const T
       for (int j = 0; j < 4; ++j) {
         T xv[NR];
         ldv<T, NR>(x + cc[j] * NR, xv);
-        T w = (T)wv[j];
-        if constexpr (is_first<Epi>::value) w *= epi.gather_scale(cc[j]);
+        if constexpr (is_first<Epi>::value) {
+          const T f = epi.gather_scale(cc[j]);
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] += w * xv[q];
+          for (int q = 0; q < NR; ++q) xv[q] *= f;
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * xv[q];
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < 4; ++j) {
+        // (fused first step: the gathered value times s0 D^-1 at its column,
+        // rounded as the stored first iterate would be)
+        T f = T(1);
+        if constexpr (is_first<Epi>::value) f = epi.gather_scale(cc[j]);
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] += (T)wv[j] * x[q * xs + cc[j]];
+        for (int q = 0; q < NR; ++q) {
+          T xv = x[q * xs + cc[j]];
+          if constexpr (is_first<Epi>::value) xv *= f;
+          acc[q] += (T)wv[j] * xv;
+        }
+      }
     }
   }
   epi(row, acc);
@@ -904,18 +949,20 @@ template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T*
     run_scalar(ex, m, st, xin, EpiCheb<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
   });
 }
-template <class T> void spmv_cheb_first_il(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
-                                           const T* dinv, double s0, double c1, double c2, int kind) {
-  require_il(nr, true);
-  const bool st = use_stencil<T>(m, true);
+template <class T> void spmv_cheb_first(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
+                                        const T* dinv, double s0, double c1, double c2, int kind, bool il) {
+  require_il(nr, il);
+  const bool st = use_stencil<T>(m, il);
   // streams: b gathered, d and x_out written, D^-1 gathered
   ProfScope ps(ex, kind,
                (st ? stencil_bytes(*m.st, sizeof(T), nr, 2) : prod_bytes(m, sizeof(T), nr, nr, 2)) +
                    (double)sizeof(T) * m.rows);
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
-    if constexpr (il_ok<NR>())
-      run_scalar(ex, m, st, b, EpiChebFirstIL<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2});
+    if constexpr (il_ok<NR>()) {
+      if (il) return run_scalar(ex, m, st, b, EpiChebFirstIL<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2});
+    }
+    run_scalar(ex, m, st, b, EpiChebFirst<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2, (size_t)m.rows});
   });
 }
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
@@ -1147,8 +1194,8 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind, int k) {
   template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int, bool);                \
   template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
                              double, int, bool);                                                         \
-  template void spmv_cheb_first_il<T>(const Exec&, const Csr&, int, const T*, T*, T*, const T*, double,   \
-                                      double, double, int);                                                                     \
+  template void spmv_cheb_first<T>(const Exec&, const Csr&, int, const T*, T*, T*, const T*, double,      \
+                                   double, double, int, bool);                                                                     \
   template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, int);                          \
   template void bsr3_cheb<T>(const Exec&, const Csr&, const T*, const T*, T*, T*, const T*, double, double, int); \
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double, int);                \
