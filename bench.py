@@ -310,6 +310,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.only_lockstep:
+        return run_lockstep(sk, torch, wl, dev, world, dist, n=args.lockstep_n)
+
     n = args.n
     V = wl.kuhn_vertices(n, JITTER, SEED)
     dofs = 3 * (2 * n + 1) ** 3 + (n + 1) ** 3
@@ -497,6 +500,14 @@ def run_ours(args):
         for S in s3:
             S.close()
 
+    lockstep = None
+    if not args.no_batched:
+        lockstep = run_lockstep(sk, torch, wl, dev, world, dist, n=args.lockstep_n)
+
+    concurrent = None
+    if not args.no_concurrent:
+        concurrent = run_concurrent(sk, torch, wl, dev, world, dist, n, V, mus, prec, args)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(sk, torch, wl, dev, world, dist)
@@ -533,10 +544,81 @@ def run_ours(args):
         "plain_fp64_same_schedule": fp64_sched,
         "mixed_error_vs_fp64_1e-12": mixed_err,
         "method2_coupled": coupled,
+        "concurrent_viscosities": concurrent,
+        "lockstep_rhs": lockstep,
         "batched": batched,
         "coupled_96": coupled96,
     }
     return line
+
+
+def run_lockstep(sk, torch, wl, dev, world, dist, n=40, rhs=4, reps=3, mu=1e-2, dt=1e-3):
+    """One instance of the batch's kind (n^3 jittered Kuhn mesh, mu = 1e-2,
+    dt = 1e-3, mixed precision, coupled FGMRES + block-LU, one V-cycle) with
+    `rhs` N(0,1) forces: one stokes_solve_multi call (the forces in lockstep)
+    against the forces solved one after another. One warm-up, then `reps`
+    timed calls each (CUDA events)."""
+    V = wl.kuhn_vertices(n, JITTER, 7)
+    opt = sk.stokes_default_options(precision=sk.PRECISION_MIXED, vcycles=1, method=sk.METHOD_COUPLED)
+    S = sk.Stokes(n, V, mu, dt, 0.0, opt, device=dev)
+    F = torch.stack([torch.as_tensor(wl.random_force(n, 50 + k), device=dev).reshape(S.n_p2, 3)
+                     for k in range(rhs)]).contiguous()
+    U = torch.empty_like(F)
+    P = torch.empty(rhs, S.n_p1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_call(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts), out
+
+    ms_multi, infos = timed_call(lambda: S.solve_multi(F, None, TOL, out=(U, P))[2])
+    ms_one, infos1 = timed_call(lambda: [S.solve(F[k], None, TOL, out=(U[k], P[k]))[2] for k in range(rhs)])
+    S.close()
+    dofs = (3 * (2 * n + 1) ** 3 + (n + 1) ** 3) * rhs
+    ms_multi = max_over_ranks(ms_multi, dist, dev)
+    ms_one = max_over_ranks(ms_one, dist, dev)
+    return {"workload": f"kuhn{n}^3-jitter0.2-P2P1-mu{mu:g}-dt{dt:g}-coupledFGMRES-{rhs}xN(0,1)", "rhs": rhs,
+            "value": world * dofs / (ms_multi / 1e3), "unit": UNIT, "ms": ms_multi,
+            "one_at_a_time": {"value": world * dofs / (ms_one / 1e3), "ms": ms_one},
+            "outer_iters": [i.outer_iters for i in infos], "outer_iters_one_at_a_time": [i.outer_iters for i in infos1],
+            "worst_residual": max(i.rel_residual for i in infos)}
+
+
+def run_concurrent(sk, torch, wl, dev, world, dist, n, V, mus, prec, args, reps=3):
+    """The main line's solves (same mesh, loads, options and tolerance) with
+    the viscosities as concurrent instances: one context, CUDA stream and host
+    thread each (StokesBatch), so one solve's latency-bound stretches (coarse
+    levels, small vector kernels, host reads) overlap another's bandwidth-bound
+    sweeps. One warm-up step, then `reps` steps timed with CUDA events."""
+    spec = [(n, V, mu, DT, 0.0) for mu in mus]
+    opt = sk.stokes_default_options(precision=prec, vcycles=args.vcycles, schur_inner_iters=args.schur_inner_iters,
+                                    format=args.format, vel_prec=args.vel_prec, schur_prec=args.schur_prec)
+    B = sk.StokesBatch(spec, opt, device=dev, host_wait=0)
+    forces = [torch.as_tensor(wl.manufactured_force(n, V, mu, DT, SEED), device=dev).reshape(1, -1, 3) for mu in mus]
+    outs, _, _ = B.solve_all(forces, TOL)
+    times, flat = [], []
+    for _ in range(reps):
+        _, infos, ms_ = B.solve_all(forces, TOL, outs)
+        times.append(ms_)
+        flat += [x for inf in infos for x in inf]
+    B.close()
+    ms = max_over_ranks(statistics.mean(times), dist, dev)
+    dofs = 3 * (2 * n + 1) ** 3 + (n + 1) ** 3
+    return {"value": job_value(world, len(mus), dofs, ms), "unit": UNIT, "ms_per_step": ms, "steps": reps,
+            "worst_residual": max(x["rel_residual"] for x in flat),
+            "failed": sum(1 for x in flat if x["status"] != 0),
+            "scheme": "the %d viscosities of one step as concurrent instances (one context + stream + host "
+                      "thread each); the main value solves them one after another" % len(mus)}
 
 
 def run_batched(sk, torch, wl, dev, world, dist, count=32, rhs=4):
@@ -661,6 +743,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-coupled", action="store_true", help="skip the Method 2 (coupled FGMRES) line")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch line")
+    ap.add_argument("--no-concurrent", action="store_true",
+                    help="skip the line with the step's viscosities solved concurrently")
+    ap.add_argument("--lockstep-n", type=int, default=40, help="mesh size of the lockstep right-hand-side line")
+    ap.add_argument("--only-lockstep", action="store_true",
+                    help="run only the lockstep right-hand-side line (profiling) and print it")
     ap.add_argument("--no-coupled96", action="store_true", help="skip the 96^3 coupled-vs-Schur comparison")
     ap.add_argument("--mus", type=float, nargs="*", default=None, help="viscosities (default 1 1e-2 1e-4)")
     ap.add_argument("--vcycles", type=int, default=1, help="V-cycles per A~_3 preconditioner application")
