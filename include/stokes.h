@@ -208,7 +208,8 @@ stokes_status stokes_solve(stokes_ctx* ctx, const double* f, const double* g,
  * once for the four systems. A last group of two or three systems is padded
  * with zero systems; a single one takes the stokes_solve path. Each system
  * meets tol on its own full residual (info[i].rel_residual);
- * info[i].outer_iters counts the outer iterations system i took part in.
+ * info[i].outer_iters counts the outer iterations system i took part in,
+ * info[i].inner_iters the lockstep inner iterations of its group.
  * Returns STOKES_OK if every system converged, else the first failing status.
  * A following stokes_adjoint uses the last system's solution.
  * 1 <= k <= 4096. */

@@ -87,17 +87,8 @@ extern "C" stokes_status stokes_apply_agamma_noalloc(stokes_ctx* c, const double
       double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta, rho = 1.0 / sigma;
       double* xa = mb;
       double* xb = xt;
-      int k = 1;
-      if (steps >= 2) {  // the first two steps in one sweep, as the allocating path
-        const double rn = 1.0 / (2.0 * sigma - rho);
-        spmv_cheb_first<double>(ex, c->MQ, 1, bx, d, xa, c->MQ_dinv64, 1.0 / theta, rn * rho, 2.0 * rn / delta,
-                                STOKES_KERNEL_SPMV_P1);
-        rho = rn;
-        k = 2;
-      } else {
-        cheb_first<double>(ex, np, 1, c->MQ_dinv64, bx, 1.0 / theta, d, xa);
-      }
-      for (; k < steps; ++k) {
+      cheb_first<double>(ex, np, 1, c->MQ_dinv64, bx, 1.0 / theta, d, xa);
+      for (int k = 1; k < steps; ++k) {
         double rn = 1.0 / (2.0 * sigma - rho);
         spmv_cheb<double>(ex, c->MQ, 1, bx, xa, d, xb, c->MQ_dinv64, rn * rho, 2.0 * rn / delta,
                           STOKES_KERNEL_SPMV_P1);

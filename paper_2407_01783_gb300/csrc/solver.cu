@@ -101,9 +101,11 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
     if (block) bsr3_cheb<T>(c.ex, M, b, xin, d, xout, dinv, c1, c2, kind);
     else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind, il);
   };
-  if (xzero && !block && steps >= 2) {
-    // the first two steps in one sweep; the output buffer is picked so that
-    // the remaining steps' ping-pong ends in x
+  if (xzero && !block && steps >= 2 && std::is_same<T, float>::value) {
+    // the first two steps in one sweep (FP32: in FP64 the extra multiplies at
+    // each gathered column load the scarce FP64 pipe more than the saved
+    // streams relieve memory); the output buffer is picked so that the
+    // remaining steps' ping-pong ends in x
     const double rn = 1.0 / (2.0 * sigma - rho);
     T* out = (steps - 2) % 2 == 0 ? x : (T*)xt;
     spmv_cheb_first<T>(c.ex, M, nr, b, d, out, dinv, 1.0 / theta, rn * rho, 2.0 * rn / delta, kind, il);
