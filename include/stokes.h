@@ -163,6 +163,15 @@ typedef struct {
                             1 sleeps until the GPU signals (blocking-sync
                             events: the better choice when more solver threads
                             than host cores wait at once, as in a batch) */
+  int vcycle_split;      /* parity-split node numbering (each x-line's even and
+                            odd nodes stored apart, so stencil gathers are
+                            contiguous; the cycle's result is bitwise the
+                            same) on the stencil-stored finest level of the
+                            velocity V-cycles: 1 (default) in the lockstep
+                            (several right-hand-side, node-interleaved)
+                            cycles, 2 in every cycle, 0 never. With one
+                            right-hand side the renumbering passes cost more
+                            than the faster gathers save (measured at 48^3) */
 } stokes_options;
 
 typedef struct {

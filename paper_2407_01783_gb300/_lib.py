@@ -43,6 +43,7 @@ class StokesOptions(C.Structure):
         ("cheb_low", C.c_double), ("cheb_high", C.c_double), ("sym_batch", C.c_int),
         ("stencil_min_rows", C.c_int),
         ("host_wait", C.c_int),
+        ("vcycle_split", C.c_int),
     ]
 
     def as_dict(self):

@@ -1003,10 +1003,11 @@ void combine_grad_div(const Exec& ex, long long nnz, const double* abs, const do
 // ---------------------------------------------------------------------------
 // stencil-structured storage (see StencilOp in internal.h)
 // ---------------------------------------------------------------------------
-StArgs stencil_args(const StencilOp& so, int block, int rows_per_thread) {
+StArgs stencil_args(const StencilOp& so, int block, int rows_per_thread, bool split) {
   StArgs a;
   std::memset(&a, 0, sizeof(a));
   a.p2 = so.p2;
+  a.split = split && so.p2 ? 1 : 0;
   a.n = so.n;
   a.ncls = so.ncls;
   a.lo = so.p2 ? 1 : 0;
@@ -1029,7 +1030,7 @@ StArgs stencil_args(const StencilOp& so, int block, int rows_per_thread) {
   a.bbeg[so.ncls] = b;
   for (int e = 0; e < so.nd; ++e) {
     for (int k = 0; k < 3; ++k) a.d[e][k] = so.d[e][k];
-    a.lin[e] = so.lin[e];
+    a.lin[e] = a.split ? so.lin_split[e] : so.lin[e];
   }
   return a;
 }
@@ -1086,6 +1087,15 @@ StencilOp* stencil_from_csr(const Exec& ex, Arena& ar, const StencilTables* st, 
       so->d[nd][1] = (signed char)dy;
       so->d[nd][2] = (signed char)dz;
       so->lin[nd] = p2 ? dx + mm * (dy + mm * dz) : dx / 2 + mm * (dy / 2 + mm * (dz / 2));
+      if (p2) {
+        // parity-split numbering: a row of this class has x-index t of parity
+        // px; its neighbour t + dx has parity (px + dx) mod 2 and sits
+        // floor((px + dx) / 2) places further along its half of the line
+        const int px = (so->q0[c][0] - 1) & 1;
+        const int pn = ((px + dx) % 2 + 2) % 2;
+        const int fx = (px + dx + 4) / 2 - 2;
+        so->lin_split[nd] = (pn - px) * n + fx + mm * (dy + mm * dz);
+      }
       ++nd;
     }
     so->S[c] = nd - so->dbeg[c];

@@ -537,6 +537,45 @@ template <class T> void to_component_major(const Exec& ex, size_t rows, int nr, 
   SK_CHECK_LAUNCH();
 }
 
+// natural <-> parity-split numbering (SplitMap), component-major [nr][rows]
+// or, with IL, between natural component-major and split interleaved
+// [rows][nr]; a thread per natural row i
+template <class T, int NR, bool IL, bool TO>
+__global__ void k_split(size_t n, SplitMap sm, const T* __restrict__ src, T* __restrict__ dst) {
+  SK_LOOP(i) {
+    const size_t j = (size_t)sm((int)i);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const size_t nat = r * n + i;
+      const size_t spl = IL ? j * NR + r : r * n + j;
+      if (TO) dst[spl] = src[nat];
+      else dst[nat] = src[spl];
+    }
+  }
+}
+template <class T, bool TO>
+static void split_launch(const Exec& ex, size_t rows, int nr, const T* src, T* dst, bool il, const SplitMap& sm) {
+  if (!rows) return;
+  ProfScope ps(ex, STOKES_KERNEL_BLAS1, 2.0 * sizeof(T) * rows * nr);
+  if (il) {
+    SK_REQUIRE(nr == 4 || nr == 12, STOKES_ERR_ARG, "interleaved vectors need 4 or 12 components");
+    if (nr == 4) k_split<T, 4, true, TO><<<SK_GRID(rows)>>>(rows, sm, src, dst);
+    else k_split<T, 12, true, TO><<<SK_GRID(rows)>>>(rows, sm, src, dst);
+  } else {
+    SK_REQUIRE(nr == 1 || nr == 3, STOKES_ERR_ARG, "split numbering: 1 or 3 components (component-major)");
+    if (nr == 1) k_split<T, 1, false, TO><<<SK_GRID(rows)>>>(rows, sm, src, dst);
+    else k_split<T, 3, false, TO><<<SK_GRID(rows)>>>(rows, sm, src, dst);
+  }
+  SK_CHECK_LAUNCH();
+}
+template <class T> void to_split(const Exec& ex, size_t rows, int nr, const T* src, T* dst, bool il, const SplitMap& sm) {
+  split_launch<T, true>(ex, rows, nr, src, dst, il, sm);
+}
+template <class T>
+void from_split(const Exec& ex, size_t rows, int nr, const T* src, T* dst, bool il, const SplitMap& sm) {
+  split_launch<T, false>(ex, rows, nr, src, dst, il, sm);
+}
+
 template <class S, class D> __global__ void k_convert(size_t n, const S* __restrict__ x, D* __restrict__ y) {
   SK_LOOP(i) {
     y[i] = (D)x[i];
@@ -644,6 +683,8 @@ void scalar_sub(const Exec& ex, double* out, const double* a, const double* b) {
   template void cheb_first_il<T>(const Exec&, size_t, int, const T*, const T*, double, T*, T*);          \
   template void to_interleaved<T>(const Exec&, size_t, int, const T*, T*);                              \
   template void to_component_major<T>(const Exec&, size_t, int, const T*, T*);                          \
+  template void to_split<T>(const Exec&, size_t, int, const T*, T*, bool, const SplitMap&);             \
+  template void from_split<T>(const Exec&, size_t, int, const T*, T*, bool, const SplitMap&);           \
   template void mdot<T>(const Exec&, const DotScratch&, int, const T* const*, const T*, size_t, double*);  \
   template void maxpy<T>(const Exec&, int, const double*, const double*, double, const T* const*, T*, size_t);
 SK_INST1(float)

@@ -443,6 +443,7 @@ void stokes_default_options(stokes_options* o) {
   o->sym_batch = 0;
   o->stencil_min_rows = 0;
   o->host_wait = 0;
+  o->vcycle_split = 1;
 }
 
 const char* stokes_status_string(int s) {
@@ -482,7 +483,7 @@ stokes_status stokes_setup(int n, const double* vertices, double mu, double dt, 
       c->opt.pass_schedule < 0 || c->opt.pass_schedule > 2 || !(c->opt.cheb_low > 0) ||
       !(c->opt.cheb_high > c->opt.cheb_low) || !std::isfinite(c->opt.cheb_high) ||
       !(c->opt.sym_batch == 0 || c->opt.sym_batch == 2 || c->opt.sym_batch == 4 || c->opt.sym_batch == 8) ||
-      c->opt.host_wait < 0 || c->opt.host_wait > 1) {
+      c->opt.host_wait < 0 || c->opt.host_wait > 1 || c->opt.vcycle_split < 0 || c->opt.vcycle_split > 2) {
     g_last_error = "stokes_setup: invalid options";
     delete c;
     return STOKES_ERR_ARG;

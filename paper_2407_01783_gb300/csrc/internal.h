@@ -114,6 +114,7 @@ struct StencilOp {
   long long total_real = 0;  // stored entries without the padding entries
   signed char d[kMaxStencil][3] = {};  // half-grid offsets of entry e
   int lin[kMaxStencil] = {};           // linear index offsets of entry e
+  int lin_split[kMaxStencil] = {};     // the same in parity-split numbering (P2 only, see SplitMap)
   int nd = 0;
   double* v64 = nullptr;
   float* v32 = nullptr;
@@ -126,13 +127,30 @@ template <> inline float* StencilOp::v<float>() const { return v32; }
 // contiguous: class c owns blocks [bbeg[c], bbeg[c+1])).
 struct StArgs {
   int p2, n, ncls, lo, hi, m, R;  // R: rows per thread of the launch using these args
+  int split;                      // rows and columns in parity-split numbering (P2 only)
   int rows[8], ext[8][3], q0[8][3], S[8], Sreal[8], dbeg[8], pext[8], prows[8];
   long long voff[8];
   int bbeg[9];
   signed char d[kMaxStencil][3];
   int lin[kMaxStencil];
 };
-StArgs stencil_args(const StencilOp& s, int block, int rows_per_thread);
+StArgs stencil_args(const StencilOp& s, int block, int rows_per_thread, bool split = false);
+
+// Parity-split numbering of the interior P2 nodes of a level (m = 2n - 1
+// points per axis): within every x-line the nodes of even x-index t come
+// first (t / 2), then those of odd t (n + t / 2); y and z strides unchanged.
+// The rows of one stencil class share the parity of t, so the neighbours a
+// warp of consecutive class rows gathers are consecutive words instead of
+// every second one. The map of a natural index i:
+struct SplitMap {
+  int m = 0, half = 0;  // points per axis; nodes of even t per line (n)
+#ifdef __CUDACC__
+  __host__ __device__ __forceinline__ int operator()(int i) const {
+    const int t = i % m;
+    return i - t + ((t & 1) ? half + (t >> 1) : (t >> 1));
+  }
+#endif
+};
 
 #ifdef __CUDACC__
 // class and row-in-class of this thread; false if past the class end
@@ -155,7 +173,11 @@ __device__ __forceinline__ void st_coords(const StArgs& a, int c, int pr, int& i
 }
 // index of half-grid node q in the matrix's index space
 __device__ __forceinline__ int st_index(const StArgs& a, int qx, int qy, int qz) {
-  if (a.p2) return (qx - 1) + a.m * ((qy - 1) + a.m * (qz - 1));
+  if (a.p2) {
+    const int t = qx - 1;
+    const int xs = a.split ? ((t & 1) ? a.n + (t >> 1) : (t >> 1)) : t;
+    return xs + a.m * ((qy - 1) + a.m * (qz - 1));
+  }
   return (qx >> 1) + a.m * ((qy >> 1) + a.m * (qz >> 1));
 }
 __device__ __forceinline__ bool st_inside(const StArgs& a, int qx, int qy, int qz) {
@@ -382,6 +404,8 @@ struct Level {
   double *A3_dinv64 = nullptr, *KQ_dinv64 = nullptr;
   float *A3_dinv32 = nullptr, *KQ_dinv32 = nullptr;
   double A3_lmax = 0, KQ_lmax = 0;  // lambda_max(D^{-1} A) estimates
+  double* A3_dinv_split64 = nullptr;  // A3 diagonal inverse in parity-split numbering (built on first use)
+  float* A3_dinv_split32 = nullptr;
   Csr P2, R2, P1, R1;               // transfers to/from level+1 (P: this <- coarse)
   // coarsest level: dense inverses (row-major)
   double *A3_cinv64 = nullptr, *KQ_cinv64 = nullptr;
@@ -452,22 +476,44 @@ void subsample_vertices(int nf, int nc, const double* Xf_host, double* Xc_host);
 // ---------------------------------------------------------------------------
 // y = A x for a scalar matrix on nr right-hand sides (nr = 1, 3, 4 or 12):
 // component-major vectors (component r of row i at r * rows + i), or with il
-// node-interleaved ones (at i * nr + r; nr = 4 or 12).
+// node-interleaved ones (at i * nr + r; nr = 4 or 12). The products below
+// that take a `split` flag run a stencil-stored P2 matrix with rows and
+// columns in parity-split numbering (SplitMap); they require stencil storage
+// in use for the given layout (stencil_in_use).
+// layout bits of the scalar products: node-interleaved vectors, parity-split
+// numbering (both need stencil storage in use for the split)
+constexpr int kLayoutIL = 1;
+constexpr int kLayoutSplit = 2;
 template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind,
-                                   bool il = false);
+                                   int layout = 0);
 // y = b - A x
 template <class T> void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind,
-                                   bool il = false);
+                                   int layout = 0);
 // y += A x
-template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il = false);
+template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, int layout = 0);
 // Chebyshev step: r = b - A xin; d = c1 d + c2 dinv r; xout = xin + d.
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin,
-                                  T* d, T* xout, const T* dinv, double c1, double c2, int kind, bool il = false);
+                                  T* d, T* xout, const T* dinv, double c1, double c2, int kind, int layout = 0);
+// true if the products of m in this precision and layout read stencil storage
+template <class T> bool stencil_in_use(const Csr& m, bool il);
+// restriction from a split-numbered fine vector: y = R x with the columns of R
+// (natural fine indices) mapped by sm; prolongation into a split-numbered fine
+// vector: y += P x with the rows of P mapped by sm
+template <class T> void restrict_split(const Exec& ex, const Csr& R, int nr, const T* x, T* y, bool il,
+                                      const SplitMap& sm);
+template <class T> void prolong_add_split(const Exec& ex, const Csr& P, int nr, const T* x, T* y, bool il,
+                                          const SplitMap& sm);
+// [nr][rows] (natural) <-> [nr][rows] (split-numbered), or with il the
+// interleaved copies to / from split numbering
+template <class T> void to_split(const Exec& ex, size_t rows, int nr, const T* src, T* dst, bool il,
+                                 const SplitMap& sm);
+template <class T> void from_split(const Exec& ex, size_t rows, int nr, const T* src, T* dst, bool il,
+                                   const SplitMap& sm);
 // the first two Chebyshev steps from x = 0 in one sweep: x1 = d1 = s0 D^-1 b
 // formed at each gathered column, then d = c1 d1 + c2 D^-1 (b - A x1),
 // xout = x1 + d (il: node-interleaved vectors, nr = 4 or 12)
 template <class T> void spmv_cheb_first(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
-                                        const T* dinv, double s0, double c1, double c2, int kind, bool il = false);
+                                        const T* dinv, double s0, double c1, double c2, int kind, int layout = 0);
 // BSR3 strain-form A: y = A x or y = b - A x (b may be null).
 template <class T> void bsr3_apply(const Exec& ex, const Csr& m, const T* x, T* y, const T* b,
                                    int kind = STOKES_KERNEL_SPMV_A);

@@ -83,10 +83,12 @@ static size_t npres(const stokes_ctx& c) { return (size_t)c.lv[0].np; }
 // ---------------------------------------------------------------------------
 // Chebyshev semi-iteration for D^{-1} M on [lmin, lmax] (Saad, Alg. 12.1)
 // ---------------------------------------------------------------------------
-// il: node-interleaved vectors (several right-hand sides, nr = 4 or 12)
+// layout: kLayoutIL (node-interleaved vectors of several right-hand sides,
+// nr = 4 or 12) and / or kLayoutSplit (parity-split numbering, dinv in it too)
 template <class T>
 static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double lmin, double lmax, int steps,
-                     const T* b, T* x, bool xzero, int kind, bool il = false) {
+                     const T* b, T* x, bool xzero, int kind, int layout = 0) {
+  const bool il = layout & kLayoutIL;
   // a 3x3-block operator (M.br == 3) has one diagonal entry per component
   const bool block = M.br == 3;
   size_t len = (size_t)M.rows * (block ? 3 : nr);
@@ -99,7 +101,7 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
   if (xzero && (steps - 1) % 2 == 1) std::swap(xa, xb);
   auto step = [&](const T* xin, T* xout, double c1, double c2) {
     if (block) bsr3_cheb<T>(c.ex, M, b, xin, d, xout, dinv, c1, c2, kind);
-    else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind, il);
+    else spmv_cheb<T>(c.ex, M, nr, b, xin, d, xout, dinv, c1, c2, kind, layout);
   };
   if (xzero && !block && steps >= 2 && std::is_same<T, float>::value) {
     // the first two steps in one sweep (FP32: in FP64 the extra multiplies at
@@ -108,7 +110,7 @@ static void cheb_run(stokes_ctx& c, const Csr& M, int nr, const T* dinv, double 
     // remaining steps' ping-pong ends in x
     const double rn = 1.0 / (2.0 * sigma - rho);
     T* out = (steps - 2) % 2 == 0 ? x : (T*)xt;
-    spmv_cheb_first<T>(c.ex, M, nr, b, d, out, dinv, 1.0 / theta, rn * rho, 2.0 * rn / delta, kind, il);
+    spmv_cheb_first<T>(c.ex, M, nr, b, d, out, dinv, 1.0 / theta, rn * rho, 2.0 * rn / delta, kind, layout);
     rho = rn;
     xa = out;
     xb = out == x ? (T*)xt : x;
@@ -145,7 +147,8 @@ template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int
     const size_t rows = (size_t)c.MQ.rows;
     Tmp<T> bi(c.pool, rows * K), xi(c.pool, rows * K);
     to_interleaved<T>(c.ex, rows, K, b, bi);
-    cheb_run<T>(c, c.MQ, K, dinv, kMassLow, kMassHigh, std::max(1, steps), bi, xi, true, STOKES_KERNEL_SPMV_P1, true);
+    cheb_run<T>(c, c.MQ, K, dinv, kMassLow, kMassHigh, std::max(1, steps), bi, xi, true, STOKES_KERNEL_SPMV_P1,
+                kLayoutIL);
     to_component_major<T>(c.ex, rows, K, xi, x);
     return;
   }
@@ -158,7 +161,8 @@ template <class T> static void mass_inverse(stokes_ctx& c, const T* b, T* x, int
 // sweep of the level matrices
 // ---------------------------------------------------------------------------
 template <class T>
-static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K = 1, bool il = false);
+static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K = 1, bool il = false,
+                   bool split = false);
 
 // Levels >= 1 are latency-bound (a few thousand rows per launch), so below
 // level 0 the V-cycle is replayed from a CUDA graph. Graph launches are not
@@ -362,14 +366,39 @@ static const Csr& level_op(const Level& L, int which) { return which == 1 ? L.KQ
 
 // residual r = b - M x of a level operator (scalar with nr components or 3x3 blocks)
 template <class T>
-static void level_resid(stokes_ctx& c, const Csr& M, int nr, const T* b, const T* x, T* r, int kind, bool il = false) {
+static void level_resid(stokes_ctx& c, const Csr& M, int nr, const T* b, const T* x, T* r, int kind, int layout = 0) {
   if (M.br == 3) bsr3_apply<T>(c.ex, M, x, r, b, kind);
-  else spmv_resid<T>(c.ex, M, nr, b, x, r, kind, il);
+  else spmv_resid<T>(c.ex, M, nr, b, x, r, kind, layout);
 }
 
-// il: node-interleaved level vectors (K > 1)
+// the finest level of Ã₃ in parity-split numbering (see SplitMap)
+static SplitMap split_map(const stokes_ctx& c) {
+  SplitMap sm;
+  sm.m = 2 * c.lv[0].n - 1;
+  sm.half = c.lv[0].n;
+  return sm;
+}
+template <class T> static const T* split_dinv(stokes_ctx& c) {
+  Level& L = c.lv[0];
+  T*& slot = *reinterpret_cast<T**>(std::is_same<T, float>::value ? (void*)&L.A3_dinv_split32
+                                                                    : (void*)&L.A3_dinv_split64);
+  if (!slot) {
+    slot = c.arena.alloc<T>(L.A3.rows);
+    to_split<T>(c.ex, (size_t)L.A3.rows, 1, pick<T>(L.A3_dinv64, L.A3_dinv32), slot, false, split_map(c));
+  }
+  return slot;
+}
+// whether velocity V-cycles of A~_3 run their finest level split-numbered
+// (option vcycle_split: 1 the interleaved lockstep cycles, 2 all)
+template <class T> static bool use_split(const stokes_ctx& c, int which, bool il) {
+  const bool wanted = c.opt.vcycle_split == 2 || (c.opt.vcycle_split == 1 && il);
+  return wanted && which == 0 && c.lv.size() >= 2 && c.lv[0].A3.st != nullptr && stencil_in_use<T>(c.lv[0].A3, il);
+}
+
+// il: node-interleaved level vectors (K > 1); split: level 0 parity-split
+// numbered (b, x and the temporaries of level 0)
 template <class T>
-static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K, bool il) {
+static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero, int K, bool il, bool split) {
   SK_REQUIRE(which != 2 || K == 1, STOKES_ERR_ARG, "block V-cycle: one right-hand side per call");
   Level& L = c.lv[l];
   const int nr = (which == 1 ? 1 : 3) * K;
@@ -384,25 +413,38 @@ static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero
     dense_apply<T>(c.ex, Minv, M.rows, nr, b, x, il);
     return;
   }
+  split = split && l == 0;
+  const int layout = (il ? kLayoutIL : 0) | (split ? kLayoutSplit : 0);
+  const SplitMap sm = split ? split_map(c) : SplitMap{};
   const T* dinv = which == 1 ? pick<T>(L.KQ_dinv64, L.KQ_dinv32)
-                             : (which == 2 ? pick<T>(L.AV_dinv64, L.AV_dinv32) : pick<T>(L.A3_dinv64, L.A3_dinv32));
+                             : (which == 2 ? pick<T>(L.AV_dinv64, L.AV_dinv32)
+                                           : (split ? split_dinv<T>(c) : pick<T>(L.A3_dinv64, L.A3_dinv32)));
   const double lhat = which == 1 ? L.KQ_lmax : (which == 2 ? L.AV_lmax : L.A3_lmax);
   double lmax = c.opt.cheb_high * lhat, lmin = c.opt.cheb_low * lhat;
   int deg = std::max(1, c.opt.cheb_degree);
   const int kind = which == 1 ? STOKES_KERNEL_SPMV_P1 : (l == 0 ? STOKES_KERNEL_SPMM_A3 : STOKES_KERNEL_SPMM_A3_COARSE);
-  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind, il);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, xzero, kind, layout);
   Level& Lc = c.lv[l + 1];
   const Csr& Mc = level_op(Lc, which);
   size_t lenc = (size_t)Mc.rows * nr;
+  // transfers from / to this level (the coarse level is always natural)
+  auto restrict_to = [&](const T* r, T* bc) {
+    if (split) restrict_split<T>(c.ex, L.R2, nr, r, bc, il, sm);
+    else spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER, il);
+  };
+  auto prolong_into = [&](const T* xc, T* xf) {
+    if (split) prolong_add_split<T>(c.ex, L.P2, nr, xc, xf, il, sm);
+    else spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, xc, xf, STOKES_KERNEL_TRANSFER, il);
+  };
   if (l == 0 && K == 1 && coarse_kernel_ok(c, which)) {
     MgProgram* P = mg_program<T>(c, which);
     {
       Tmp<T> r(c.pool, len);
-      level_resid<T>(c, M, nr, b, x, r, kind);
-      spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, (T*)P->b, STOKES_KERNEL_TRANSFER);
+      level_resid<T>(c, M, nr, b, x, r, kind, layout);
+      restrict_to(r, (T*)P->b);
     }
     P->launch(c.ex);
-    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, (const T*)P->x, x, STOKES_KERNEL_TRANSFER);
+    prolong_into((const T*)P->x, x);
   } else if (l == 0 && K == 1 && coarse_graph_ok(c, which)) {
     auto& G = c.cgraph[which][std::is_same<T, float>::value ? 1 : 0];
     if (!G.b) {
@@ -412,34 +454,40 @@ static void vcycle(stokes_ctx& c, int which, int l, const T* b, T* x, bool xzero
     }
     {
       Tmp<T> r(c.pool, len);
-      level_resid<T>(c, M, nr, b, x, r, kind);
-      spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, (T*)G.b, STOKES_KERNEL_TRANSFER);
+      level_resid<T>(c, M, nr, b, x, r, kind, layout);
+      restrict_to(r, (T*)G.b);
     }
     coarse_run<T>(c, which, G);
-    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, (const T*)G.x, x, STOKES_KERNEL_TRANSFER);
+    prolong_into((const T*)G.x, x);
   } else {
     Tmp<T> r(c.pool, len);
-    level_resid<T>(c, M, nr, b, x, r, kind, il);
+    level_resid<T>(c, M, nr, b, x, r, kind, layout);
     Tmp<T> bc(c.pool, lenc), xc(c.pool, lenc);
-    spmv_store<T>(c.ex, which == 1 ? L.R1 : L.R2, nr, r, bc, STOKES_KERNEL_TRANSFER, il);
+    restrict_to(r, bc);
     vcycle<T>(c, which, l + 1, bc, xc, true, K, il);
-    spmv_add<T>(c.ex, which == 1 ? L.P1 : L.P2, nr, xc, x, STOKES_KERNEL_TRANSFER, il);
+    prolong_into(xc, x);
   }
-  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind, il);
+  cheb_run<T>(c, M, nr, dinv, lmin, lmax, deg, b, x, false, kind, layout);
 }
 
 // K > 1: the cycles run on node-interleaved copies (a row's 3K or K values
 // contiguous, gathered as 16-byte vectors by the sparse kernels); b and x
 // stay component-major K-blocks
+// With a parity-split finest level (use_split) b is renumbered on the way in
+// and x on the way out (one pass each, fused with the interleaving for K > 1).
 template <class T> static void vcycles_plain(stokes_ctx& c, int which, const T* b, T* x, int cycles, int K = 1) {
-  if (K > 1) {
+  const bool il = K > 1;
+  const bool split = use_split<T>(c, which, il);
+  if (il || split) {
     const size_t rows = (size_t)level_op(c.lv[0], which).rows;
     const int nr = (which == 1 ? 1 : 3) * K;
     Tmp<T> bi(c.pool, rows * nr), xi(c.pool, rows * nr);
-    to_interleaved<T>(c.ex, rows, nr, b, bi);
-    vcycle<T>(c, which, 0, bi, xi, true, K, true);
-    for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, bi, xi, false, K, true);
-    to_component_major<T>(c.ex, rows, nr, xi, x);
+    if (split) to_split<T>(c.ex, rows, nr, b, bi, il, split_map(c));
+    else to_interleaved<T>(c.ex, rows, nr, b, bi);
+    vcycle<T>(c, which, 0, bi, xi, true, K, il, split);
+    for (int k = 1; k < cycles; ++k) vcycle<T>(c, which, 0, bi, xi, false, K, il, split);
+    if (split) from_split<T>(c.ex, rows, nr, xi, x, il, split_map(c));
+    else to_component_major<T>(c.ex, rows, nr, xi, x);
     return;
   }
   vcycle<T>(c, which, 0, b, x, true, K);

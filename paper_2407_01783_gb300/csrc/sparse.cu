@@ -331,6 +331,24 @@ template <class T, int NR> struct EpiChebFirst {
 template <class E, class = void> struct is_first : std::false_type {};
 template <class E> struct is_first<E, std::void_t<decltype(E::first)>> : std::integral_constant<bool, E::first> {};
 
+// Column / row renumbering around another epilogue (the transfers next to a
+// parity-split finest level): WithColMap maps every column index the kernel
+// reads through sm before the gather; WithRowMap stores row i's result at
+// row sm(i).
+template <class E> struct WithColMap : E {
+  SplitMap sm;
+  static constexpr bool colmap = true;
+};
+template <class E> struct WithRowMap : E {
+  SplitMap sm;
+  __device__ __forceinline__ void operator()(int row, const typename std::remove_pointer<decltype(E::y)>::type* acc)
+      const {
+    E::operator()(sm(row), acc);
+  }
+};
+template <class E, class = void> struct has_colmap : std::false_type {};
+template <class E> struct has_colmap<E, std::void_t<decltype(E::colmap)>> : std::integral_constant<bool, E::colmap> {};
+
 template <int G, class T, int NR>
 __device__ __forceinline__ void group_reduce(T* acc) {
 #pragma unroll
@@ -372,6 +390,7 @@ __global__ void __launch_bounds__(256) k_csr(int rows, const int* __restrict__ r
         const bool ok = kk < e;
         const int ks = ok ? kk : e - 1;
         c[u] = col[ks];
+        if constexpr (has_colmap<Epi>::value) c[u] = epi.sm(c[u]);
         const T av = (T)val[ks];
         a[u] = ok ? av : T(0);
       }
@@ -801,9 +820,10 @@ __global__ void __launch_bounds__(SK_ST_BLOCK) k_stencil(const StArgs a, const T
 }
 
 template <class T, class Epi>
-static void launch_stencil(const Exec& ex, const StencilOp& so, int nr, const T* x, const Epi& epi) {
+static void launch_stencil(const Exec& ex, const StencilOp& so, int nr, const T* x, const Epi& epi,
+                           bool split = false) {
   const int bs = SK_ST_BLOCK;
-  StArgs a = stencil_args(so, bs, kStencilRows);
+  StArgs a = stencil_args(so, bs, kStencilRows, split);
   int grid = a.bbeg[so.ncls];
   if (grid == 0) return;
   size_t xs = 0;
@@ -892,49 +912,55 @@ template <int NR> static constexpr bool il_ok() { return NR % 4 == 0; }
 static void require_il(int nr, bool il) {
   SK_REQUIRE(!il || nr % 4 == 0, STOKES_ERR_ARG, "interleaved vectors need 4 or 12 components");
 }
-template <class T, class E> static void run_scalar(const Exec& ex, const Csr& m, bool st, const T* x, const E& e) {
-  if (st) launch_stencil(ex, *m.st, E::nr, x, e);
+template <class T, class E>
+static void run_scalar(const Exec& ex, const Csr& m, bool st, const T* x, const E& e, bool split = false) {
+  SK_REQUIRE(!split || (st && m.st->p2), STOKES_ERR_ARG, "parity-split products need P2 stencil storage");
+  if (st) launch_stencil(ex, *m.st, E::nr, x, e, split);
   else launch(ex, m, SH_CSR, x, e, m.group);
 }
-template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il) {
+template <class T> void spmv_store(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, int layout) {
+  const bool il = layout & kLayoutIL, split = layout & kLayoutSplit;
   require_il(nr, il);
   const bool st = use_stencil<T>(m, il);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 0) : prod_bytes(m, sizeof(T), nr, nr, 0));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
     if constexpr (il_ok<NR>()) {
-      if (il) return run_scalar(ex, m, st, x, EpiStoreIL<T, NR>{y});
+      if (il) return run_scalar(ex, m, st, x, EpiStoreIL<T, NR>{y}, split);
     }
-    run_scalar(ex, m, st, x, EpiStore<T, NR>{y, (size_t)m.rows});
+    run_scalar(ex, m, st, x, EpiStore<T, NR>{y, (size_t)m.rows}, split);
   });
 }
-template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, bool il) {
+template <class T> void spmv_add(const Exec& ex, const Csr& m, int nr, const T* x, T* y, int kind, int layout) {
+  const bool il = layout & kLayoutIL, split = layout & kLayoutSplit;
   require_il(nr, il);
   const bool st = use_stencil<T>(m, il);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
     if constexpr (il_ok<NR>()) {
-      if (il) return run_scalar(ex, m, st, x, EpiAddIL<T, NR>{y});
+      if (il) return run_scalar(ex, m, st, x, EpiAddIL<T, NR>{y}, split);
     }
-    run_scalar(ex, m, st, x, EpiAdd<T, NR>{y, (size_t)m.rows});
+    run_scalar(ex, m, st, x, EpiAdd<T, NR>{y, (size_t)m.rows}, split);
   });
 }
 template <class T>
-void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind, bool il) {
+void spmv_resid(const Exec& ex, const Csr& m, int nr, const T* b, const T* x, T* y, int kind, int layout) {
+  const bool il = layout & kLayoutIL, split = layout & kLayoutSplit;
   require_il(nr, il);
   const bool st = use_stencil<T>(m, il);
   ProfScope ps(ex, kind, st ? stencil_bytes(*m.st, sizeof(T), nr, 1) : prod_bytes(m, sizeof(T), nr, nr, 1));
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
     if constexpr (il_ok<NR>()) {
-      if (il) return run_scalar(ex, m, st, x, EpiResidIL<T, NR>{b, y});
+      if (il) return run_scalar(ex, m, st, x, EpiResidIL<T, NR>{b, y}, split);
     }
-    run_scalar(ex, m, st, x, EpiResid<T, NR>{b, y, (size_t)m.rows});
+    run_scalar(ex, m, st, x, EpiResid<T, NR>{b, y, (size_t)m.rows}, split);
   });
 }
 template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T* b, const T* xin, T* d, T* xout,
-                                  const T* dinv, double c1, double c2, int kind, bool il) {
+                                  const T* dinv, double c1, double c2, int kind, int layout) {
+  const bool il = layout & kLayoutIL, split = layout & kLayoutSplit;
   require_il(nr, il);
   const bool st = use_stencil<T>(m, il);
   // streams: b, x_in (own row), d read, d write, x_out write, dinv
@@ -944,13 +970,14 @@ template <class T> void spmv_cheb(const Exec& ex, const Csr& m, int nr, const T*
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
     if constexpr (il_ok<NR>()) {
-      if (il) return run_scalar(ex, m, st, xin, EpiChebIL<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2});
+      if (il) return run_scalar(ex, m, st, xin, EpiChebIL<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2}, split);
     }
-    run_scalar(ex, m, st, xin, EpiCheb<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows});
+    run_scalar(ex, m, st, xin, EpiCheb<T, NR>{b, xin, d, xout, dinv, (T)c1, (T)c2, (size_t)m.rows}, split);
   });
 }
 template <class T> void spmv_cheb_first(const Exec& ex, const Csr& m, int nr, const T* b, T* d, T* xout,
-                                        const T* dinv, double s0, double c1, double c2, int kind, bool il) {
+                                        const T* dinv, double s0, double c1, double c2, int kind, int layout) {
+  const bool il = layout & kLayoutIL, split = layout & kLayoutSplit;
   require_il(nr, il);
   const bool st = use_stencil<T>(m, il);
   // streams: b gathered, d and x_out written, D^-1 gathered
@@ -960,9 +987,35 @@ template <class T> void spmv_cheb_first(const Exec& ex, const Csr& m, int nr, co
   with_nr(nr, [&](auto NRc) {
     constexpr int NR = decltype(NRc)::value;
     if constexpr (il_ok<NR>()) {
-      if (il) return run_scalar(ex, m, st, b, EpiChebFirstIL<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2});
+      if (il) return run_scalar(ex, m, st, b, EpiChebFirstIL<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2}, split);
     }
-    run_scalar(ex, m, st, b, EpiChebFirst<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2, (size_t)m.rows});
+    run_scalar(ex, m, st, b, EpiChebFirst<T, NR>{b, d, xout, dinv, (T)s0, (T)c1, (T)c2, (size_t)m.rows}, split);
+  });
+}
+template <class T> bool stencil_in_use(const Csr& m, bool il) { return use_stencil<T>(m, il); }
+
+template <class T>
+void restrict_split(const Exec& ex, const Csr& R, int nr, const T* x, T* y, bool il, const SplitMap& sm) {
+  require_il(nr, il);
+  ProfScope ps(ex, STOKES_KERNEL_TRANSFER, prod_bytes(R, sizeof(T), nr, nr, 0));
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    if constexpr (il_ok<NR>()) {
+      if (il) return launch(ex, R, SH_CSR, x, WithColMap<EpiStoreIL<T, NR>>{{y}, sm}, R.group);
+    }
+    launch(ex, R, SH_CSR, x, WithColMap<EpiStore<T, NR>>{{y, (size_t)R.rows}, sm}, R.group);
+  });
+}
+template <class T>
+void prolong_add_split(const Exec& ex, const Csr& P, int nr, const T* x, T* y, bool il, const SplitMap& sm) {
+  require_il(nr, il);
+  ProfScope ps(ex, STOKES_KERNEL_TRANSFER, prod_bytes(P, sizeof(T), nr, nr, 1));
+  with_nr(nr, [&](auto NRc) {
+    constexpr int NR = decltype(NRc)::value;
+    if constexpr (il_ok<NR>()) {
+      if (il) return launch(ex, P, SH_CSR, x, WithRowMap<EpiAddIL<T, NR>>{{y}, sm}, P.group);
+    }
+    launch(ex, P, SH_CSR, x, WithRowMap<EpiAdd<T, NR>>{{y, (size_t)P.rows}, sm}, P.group);
   });
 }
 template <class T> void bsr3_cheb(const Exec& ex, const Csr& m, const T* b, const T* xin, T* d, T* xout,
@@ -1189,13 +1242,16 @@ void autotune_group(const Exec& ex, Csr& m, int nr, int kind, int k) {
 }
 
 #define SK_INST(T)                                                                                        \
-  template void spmv_store<T>(const Exec&, const Csr&, int, const T*, T*, int, bool);                          \
-  template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int, bool);                            \
-  template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int, bool);                \
+  template void spmv_store<T>(const Exec&, const Csr&, int, const T*, T*, int, int);                          \
+  template void spmv_add<T>(const Exec&, const Csr&, int, const T*, T*, int, int);                            \
+  template void spmv_resid<T>(const Exec&, const Csr&, int, const T*, const T*, T*, int, int);                \
   template void spmv_cheb<T>(const Exec&, const Csr&, int, const T*, const T*, T*, T*, const T*, double, \
-                             double, int, bool);                                                         \
+                             double, int, int);                                                         \
   template void spmv_cheb_first<T>(const Exec&, const Csr&, int, const T*, T*, T*, const T*, double,      \
-                                   double, double, int, bool);                                                                     \
+                                   double, double, int, int);                                          \
+  template bool stencil_in_use<T>(const Csr&, bool);                                                     \
+  template void restrict_split<T>(const Exec&, const Csr&, int, const T*, T*, bool, const SplitMap&);   \
+  template void prolong_add_split<T>(const Exec&, const Csr&, int, const T*, T*, bool, const SplitMap&);                                                                     \
   template void bsr3_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, int);                          \
   template void bsr3_cheb<T>(const Exec&, const Csr&, const T*, const T*, T*, T*, const T*, double, double, int); \
   template void b_apply<T>(const Exec&, const Csr&, const T*, T*, const T*, double, int);                \
