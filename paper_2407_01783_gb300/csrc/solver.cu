@@ -378,10 +378,11 @@ static SplitMap split_map(const stokes_ctx& c) {
   sm.half = c.lv[0].n;
   return sm;
 }
+static double*& split_dinv_slot(Level& L, double*) { return L.A3_dinv_split64; }
+static float*& split_dinv_slot(Level& L, float*) { return L.A3_dinv_split32; }
 template <class T> static const T* split_dinv(stokes_ctx& c) {
   Level& L = c.lv[0];
-  T*& slot = *reinterpret_cast<T**>(std::is_same<T, float>::value ? (void*)&L.A3_dinv_split32
-                                                                    : (void*)&L.A3_dinv_split64);
+  T*& slot = split_dinv_slot(L, (T*)nullptr);
   if (!slot) {
     slot = c.arena.alloc<T>(L.A3.rows);
     to_split<T>(c.ex, (size_t)L.A3.rows, 1, pick<T>(L.A3_dinv64, L.A3_dinv32), slot, false, split_map(c));
