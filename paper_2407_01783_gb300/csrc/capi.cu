@@ -112,6 +112,9 @@ struct PhaseClock {
   std::chrono::steady_clock::time_point t;
   explicit PhaseClock(stokes_ctx& cc) : c(cc), t(std::chrono::steady_clock::now()) {}
   void mark(int phase) {
+    static const char* const names[STOKES_SETUP_PHASES] = {"setup: assembly", "setup: storage", "setup: coarse",
+                                                           "setup: spectra",  "setup: copies",  "setup: tuning"};
+    nvtxMarkA(names[phase]);  // the end of the phase on a profiler's timeline
     SK_CUDA(cudaStreamSynchronize(c.ex.s));
     const auto now = std::chrono::steady_clock::now();
     c.setup_ms[phase] += std::chrono::duration<double, std::milli>(now - t).count();
@@ -120,6 +123,7 @@ struct PhaseClock {
 };
 
 void setup_context(stokes_ctx* cp, int n, const double* Xh) {
+  NvtxRange range("stokes_setup");
   stokes_ctx& c = *cp;
   PhaseClock clock(c);
   c.n = n;

@@ -1014,6 +1014,7 @@ static void method2(stokes_ctx& c, const T* rF, const T* rg, T* dU, T* dP, doubl
 template <class T>
 static void correction(stokes_ctx& c, const double* rF, const double* rg, double* U, double* P, double eta,
                        double tol_in) {
+  NvtxRange range(std::is_same<T, float>::value ? "correction pass (FP32)" : "correction pass (FP64)");
   const size_t nv = nvel(c), np = npres(c);
   Tmp<T> dU(c.pool, nv), dP(c.pool, np);
   const T* rFt;
@@ -1162,6 +1163,7 @@ static int solve_reduced(stokes_ctx& c, const double* F, const double* g, double
 
 int solve_context(stokes_ctx* cp, const double* f, const double* g, double tol, double* u, double* p,
                   stokes_info* info) {
+  NvtxRange range("stokes_solve");
   stokes_ctx& c = *cp;
   auto t0 = std::chrono::steady_clock::now();
   c.sc.top = 0;
@@ -1725,6 +1727,7 @@ static void full_residual_k(stokes_ctx& c, int K, const double* F, const double*
 template <class T>
 static void correction_k(stokes_ctx& c, int K, const double* R, double* X, const double* eta, double tol_in,
                          unsigned live, int* its) {
+  NvtxRange range(std::is_same<T, float>::value ? "lockstep correction pass (FP32)" : "lockstep correction pass (FP64)");
   const size_t KN = (size_t)K * (nvel(c) + npres(c));
   Tmp<T> dX(c.pool, KN);
   Tmp<T> R32(c.pool, std::is_same<T, double>::value ? 1 : KN);
@@ -1847,6 +1850,7 @@ static void solve_reduced_k(stokes_ctx& c, int K, const double* F, const double*
 // systems; a single one takes the one-system path).
 int solve_multi_context(stokes_ctx* cp, int K, const double* f, const double* g, double tol, double* u, double* p,
                         stokes_info* info) {
+  NvtxRange range("stokes_solve_multi");
   stokes_ctx& c = *cp;
   auto t0 = std::chrono::steady_clock::now();
   c.sc.top = 0;
@@ -1904,6 +1908,7 @@ int solve_multi_context(stokes_ctx* cp, int K, const double* f, const double* g,
 // (the augmented-Lagrangian form has the same solution for every gamma).
 int adjoint_context(stokes_ctx* cp, const double* dJdu, const double* dJdp, double tol, double* dJdf,
                     double* dJdg, double* dJdmu, stokes_info* info) {
+  NvtxRange range("stokes_adjoint");
   stokes_ctx& c = *cp;
   auto t0 = std::chrono::steady_clock::now();
   const size_t nv = nvel(c), np = npres(c);
