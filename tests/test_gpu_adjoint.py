@@ -25,13 +25,13 @@ pytestmark = pytest.mark.gpu
 N, MU, DT = 4, 0.3, 0.05
 
 
-def setup_case(seed=31):
+def setup_case(seed=31, n=N):
     sk = gpu_module()
-    V = wl.kuhn_vertices(N, 0.2, seed)
-    f = wl.random_force(N, seed + 1)
+    V = wl.kuhn_vertices(n, 0.2, seed)
+    f = wl.random_force(n, seed + 1)
     rng = np.random.default_rng(seed)
-    c = rng.standard_normal(((2 * N + 1) ** 3, 3))
-    d = rng.standard_normal((N + 1) ** 3)
+    c = rng.standard_normal(((2 * n + 1) ** 3, 3))
+    d = rng.standard_normal((n + 1) ** 3)
     return sk, V, f, c, d
 
 
@@ -40,12 +40,13 @@ def J(sk, S, f, c, d, tol=1e-13):
     return float((host(u) * c).sum() + host(p) @ d), host(u), host(p)
 
 
-def test_adjoint_matches_oracle_adjoint():
-    sk, V, f, c, d = setup_case()
-    S = sk.Stokes(N, V, MU, DT)
+@pytest.mark.parametrize("n", [4, 8])
+def test_adjoint_matches_oracle_adjoint(n):
+    sk, V, f, c, d = setup_case(n=n)
+    S = sk.Stokes(n, V, MU, DT)
     J0, u, p = J(sk, S, f, c, d)
     dJdf, dJdg, dmu, info = S.adjoint(cuda(c), cuda(d), 1e-13)
-    orc = StokesSystem(KuhnMesh(N, V), MU, DT)
+    orc = StokesSystem(KuhnMesh(n, V), MU, DT)
     Kb = bordered_matrix(orc)
     rhs = np.concatenate([orc.restrict_velocity(c), d, [0.0]])
     lam = spla.splu(Kb.T.tocsc()).solve(rhs)
