@@ -60,3 +60,25 @@ def test_options_struct_layout_matches_header():
     body = body[: body.index("} stokes_options;")]
     fields = re.findall(r"\b(?:int|double)\s+([a-z_0-9]+);", body)
     assert fields == [f for f, _ in L.StokesOptions._fields_]
+
+
+def test_lockstep_and_wait_options_validated_on_host(lib):
+    """Defaults of the lockstep-related options, rejection of out-of-range
+    values and of bad stokes_solve_multi arguments, all before any CUDA call."""
+    import numpy as np
+    from paper_2407_01783_gb300 import _lib as L
+    o = L.StokesOptions()
+    lib.stokes_default_options(C.byref(o))
+    assert o.host_wait == 0 and o.vcycle_split == 1
+    V = np.zeros((3 ** 3, 3))
+    h = C.c_void_p()
+    lib.stokes_setup.argtypes = [C.c_int, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                 C.POINTER(L.StokesOptions), C.c_void_p, C.POINTER(C.c_void_p)]
+    for field, bad in (("host_wait", 2), ("vcycle_split", 3), ("vcycle_split", -1)):
+        ob = L.StokesOptions.from_buffer_copy(o)
+        setattr(ob, field, bad)
+        assert lib.stokes_setup(2, V.ctypes.data, 1.0, 1.0, 0.0, C.byref(ob), None, C.byref(h)) == -1, field
+        assert not h.value
+    lib.stokes_solve_multi.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
+    assert lib.stokes_solve_multi(None, 4, None, None, 1e-8, None, None, None) == -1
